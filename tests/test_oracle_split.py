@@ -1,0 +1,127 @@
+"""Pins for the oracle's kernel split (Sec. 2, Eq. 1-8) and its error/cost models."""
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial.legendre import leggauss
+from scipy.integrate import quad
+
+import oracle as O
+from paper_1409_4441_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_split_identity_before_truncation():
+    """K_harm (l <= l_cut) applied harmonically plus the remainder applied in real
+    space over the whole sphere reproduces the full convolution (Eq. 1 before
+    truncation)."""
+    nside, lmax, lcut = 8, 23, 9
+    b = O.gaussian_beam(lmax, np.radians(15.0))
+    sp = O.split_sharp(b, lcut)
+    m = inputs.white_noise_map(nside, 31)
+    kh = np.zeros(lmax + 1); kh[: lcut + 1] = sp["k_harm"]
+    harm = O.sht_conv(nside, m, kh)
+    real, _ = O.brute_conv(nside, m, np.pi, c=sp["c_real"])
+    full = O.sht_conv(nside, m, b)
+    np.testing.assert_allclose(harm + real, full, atol=1e-12 * np.abs(full).max())
+
+
+def test_operator_columns_are_exact_transforms():
+    """A_{l j} = 2 pi int_{cos tc}^1 f_j(z) P_l(z) dz, checked with adaptive quadrature."""
+    lmax, tc = 60, np.radians(20.0)
+    zj, wj, Pj, A = O.real_space_basis(lmax, tc, oversample=2)
+    zc = np.cos(tc)
+    from scipy.special import eval_legendre
+    for j in (0, zj.size // 2, zj.size - 1):
+        # f_j = w_j sum_l (2l+1)/2 P_l(z_j) P_l(z) = 2 pi w_j * legendre_sum(P(z_j))
+        cj = Pj[j]
+        for l in (0, 7, 33, 60):
+            f = lambda z: 2 * np.pi * wj[j] * O.legendre_sum(cj, [z])[0] * eval_legendre(l, z)
+            val, _ = quad(f, zc, 1.0, limit=400, epsabs=1e-14, epsrel=1e-12)
+            assert A[l, j] == pytest.approx(2 * np.pi * val, rel=1e-9, abs=1e-14)
+
+
+def test_real_coefficients_transform_to_model():
+    """The applied real-space kernel (Legendre sum of c_real truncated at theta_cut)
+    has exactly the l-space transform P Khat_theta used in the fit."""
+    lmax, lcut, tc = 191, 40, np.radians(6.0)
+    b = O.gaussian_beam(lmax, np.radians(2.0))
+    sp = O.split_lsq(b, lcut, tc, cl_in=inputs.cl_grf(lmax))
+    x, w = leggauss(4 * (lmax + 1))
+    zc = np.cos(tc)
+    z = zc + (x + 1) * (1 - zc) / 2
+    w = w * (1 - zc) / 2
+    Kr = O.legendre_sum(sp["c_real"], z)
+    tr = 2 * np.pi * (O.legendre_matrix(lmax, z).T @ (w * Kr))
+    kh = np.zeros(lmax + 1); kh[: lcut + 1] = sp["k_harm"]
+    np.testing.assert_allclose(kh + tr, sp["K_tilde"], atol=1e-10)
+
+
+def test_lsq_recovers_representable_kernel():
+    lmax, lcut, tc = 127, 30, np.radians(12.0)
+    zj, wj, Pj, A = O.real_space_basis(lmax, tc)
+    g = np.random.default_rng(4)
+    x0 = g.standard_normal(zj.size) * 1e3
+    K = A @ x0
+    K[: lcut + 1] += g.standard_normal(lcut + 1)
+    sp = O.split_lsq(K, lcut, tc, rcond=1e-13)
+    assert np.abs(sp["K_tilde"] - K).max() < 1e-7 * np.abs(K).max()
+
+
+def test_low_l_rows_fit_exactly_and_error_models():
+    """Fig. 5's first regime: K~ = K below l_cut; Eq. 2/6/10 closed forms."""
+    lmax, lcut, tc = 383, 64, np.radians(3.0)
+    b = O.gaussian_beam(lmax, np.radians(1.0))
+    cl = inputs.cl_grf(lmax)
+    sp = O.split_lsq(b, lcut, tc, cl_in=cl)
+    assert np.abs(sp["K_tilde"][: lcut + 1] - b[: lcut + 1]).max() < 1e-9
+    # Eq. 6 with K~ = K (1 + eps) and flat C: sigma = alpha * eps exactly
+    eps = 3e-6
+    assert O.frac_error(b, b * (1 + eps), alpha=5.0) == pytest.approx(5 * eps, rel=1e-9)
+    assert O.frac_error(b, b * (1 + eps), cl_in=cl, alpha=1.0) == pytest.approx(eps, rel=1e-9)
+    # Eq. 2 with a single-l error
+    kt = b.copy(); kt[10] += 0.01
+    assert O.sigma_rms(b, kt) == pytest.approx(np.sqrt(1e-4 * 21 / (4 * np.pi)), rel=1e-12)
+    # Eq. 10
+    np.testing.assert_allclose(O.rel_error_l(b, b * (1 - 1e-5)), -5.0, atol=1e-9)
+
+
+def test_error_decreases_with_lcut_and_theta_cut():
+    """The binary search of Sec. 2 assumes the error falls as l_cut grows."""
+    lmax = 383
+    b = O.gaussian_beam(lmax, np.radians(40 / 60))
+    cl = inputs.cl_grf(lmax)
+    tc = np.radians(150 / 60)
+    errs = [O.frac_error(b, O.split_lsq(b, lc, tc, cl)["K_tilde"], cl) for lc in (16, 48, 96, 160, 240)]
+    assert all(e2 <= e1 * 1.05 for e1, e2 in zip(errs, errs[1:]))
+    assert errs[-1] < errs[0] / 10
+
+
+def test_scan_returns_cheapest_feasible_pair():
+    lmax = 191
+    b = O.gaussian_beam(lmax, np.radians(1.5))
+    cl = inputs.cl_grf(lmax)
+    grid = np.radians(np.array([150, 240, 330]) / 60)
+    best, table = O.scan_split(b, grid, bound=1e-4, cl_in=cl)
+    assert best is not None
+    feas = [r for r in table if r[1] is not None]
+    assert best[3] == min(r[3] for r in feas)
+    for th, lc, e, cost in feas:
+        assert e <= 1e-4
+        if lc > 0:  # minimality of the binary search
+            sp = O.split_lsq(b, lc - 1, th, cl)
+            assert O.frac_error(b, sp["K_tilde"], cl) > 1e-4
+
+
+def test_cost_models_reproduce_paper_speedups():
+    """Eq. 7-8 at Table 1's cuts give the 12-15x plateau and 160 s -> ~12 s (Sec. 3)."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table1_cuts.txt"))
+    assert O.t_cpu_eq8(4096, 4096) == pytest.approx(160.0)
+    sp = []
+    for fwhm, lcut, th in rows:
+        wall = max(O.t_gpu_eq7(th), O.t_cpu_eq8(lcut, 4096))
+        sp.append(160.0 / wall)
+    sp = np.array(sp)
+    assert sp[0] == pytest.approx(12.5, abs=0.1)  # 7 arcmin: 160 s -> 12.8 s
+    assert np.all(sp >= 12.0) and np.all(sp[:4] <= 15.0)
