@@ -1,0 +1,318 @@
+"""Benchmark: real-space convolution of the Planck-resolution workload.
+
+Workload: HEALPix nside 2048 (50.3M pixels) FP32 map, l_max 4096, 5' Gaussian
+beam, least-squares split at l_cut 1024, theta_cut 240' (Sec. 2-3 sizes).  One
+step = one real-space convolution of one map (the whole hot path).  Metric:
+pixel-pair interactions per second (and maps per second) over the timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank convolves its own map (independent problems, weak
+scaling); timing is the maximum over ranks.  `--impl reference` times the FP64
+CPU oracle (all-pairs brute force) on a bounded sample of output pixels of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1409_4441_gb300 import inputs  # noqa: E402
+
+ARC = inputs.ARCMIN
+WORKLOAD = dict(nside=2048, lmax=4096, fwhm=5.0 * ARC, lcut=1024, theta_cut=240.0 * ARC)
+METRIC = "pixel-pair interactions/s and maps/s at nside=2048 vs roofline, at 1e-5 C_l rms err"
+UNIT = "pairs/s"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload_desc(extra=None):
+    d = {"workload": "nside-2048 real-space convolution: 50.3M-pixel FP32 map, l_max 4096, "
+                     "5' Gaussian beam, least-squares split l_cut 1024, theta_cut 240', "
+                     "white-noise input",
+         "nside": WORKLOAD["nside"], "lmax": WORKLOAD["lmax"], "fwhm_arcmin": 5.0,
+         "l_cut": WORKLOAD["lcut"], "theta_cut_arcmin": 240.0,
+         "l2": "inputs larger than L2 (201 MB map in, 201 MB out)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        pass
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(n_pix: int, seed: int, c, n_int: int, m64):
+    """Time the FP64 oracle on n_pix sampled output pixels; returns (pairs, seconds)."""
+    import oracle as O
+    nside, tc = WORKLOAD["nside"], WORKLOAD["theta_cut"]
+    pix = inputs.rng(seed).choice(O.npix(nside), size=n_pix, replace=False)
+    tab = O.hermite_nodes(c, tc, n_int)
+    t0 = time.perf_counter()
+    O.brute_conv(nside, m64, tc, table=tab, out_pix=pix)
+    dt = time.perf_counter() - t0
+    pairs = int(O.count_pairs(nside, tc, out_pix=pix).sum())
+    return pairs, dt
+
+
+def sharp_coeffs():
+    b = inputs.gaussian_beam(WORKLOAD["lmax"], WORKLOAD["fwhm"])
+    c = b.copy()
+    c[: WORKLOAD["lcut"] + 1] = 0.0
+    return c
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, on the host cores, bounded samples of the workload."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    nside = WORKLOAD["nside"]
+    m64 = inputs.white_noise_map(nside, inputs.seed_for(3)).astype(np.float32).astype(np.float64)
+    c = sharp_coeffs()
+    n_int = 4368  # the library's automatic table size for this workload
+    n_pix = args.ref_pixels
+    cores = os.cpu_count()
+    for w in range(args.warmup):
+        oracle_sample(max(8, n_pix // 8), 7 + w, c, n_int, m64)
+    tot_pairs, tot_t = 0, 0.0
+    for s in range(args.steps):
+        p, t = oracle_sample(n_pix, 100 + s, c, n_int, m64)
+        tot_pairs += p
+        tot_t += t
+    v = tot_pairs / tot_t
+    sample = f"{args.steps} steps x {n_pix} random output pixels of the nside-2048 map"
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc({"sample": sample}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1409_4441_gb300 import ksconv as K
+
+    nside, lmax, lcut, tc = (WORKLOAD[k] for k in ("nside", "lmax", "lcut", "theta_cut"))
+    npix = 12 * nside * nside
+    b = inputs.gaussian_beam(lmax, WORKLOAD["fwhm"])
+    cl = inputs.cl_grf(lmax)
+    t0 = time.perf_counter()
+    sp = K.make_split(b, nside, lcut, tc, cl_in=cl)
+    t_split = time.perf_counter() - t0
+    n_pairs = K.count_pairs(sp)
+    info = K.split_info(sp)
+
+    m = inputs.white_noise_map(nside, inputs.seed_for(3, rank)).astype(np.float32)
+    x = torch.tensor(m, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        K.conv_real(sp, x, y)
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            K.conv_real(sp, x, y)
+            evs[i][1].record(stream)
+        t_end.record(stream)
+        barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    launch_ms = [a.elapsed_time(b_) for a, b_ in evs]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+
+    # end to end through the host-pointer entry point (pinned host buffers)
+    hin = torch.from_numpy(m).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(max(1, min(args.warmup, 2))):
+        K.conv_real_host(sp, hin, hout)
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        K.conv_real_host(sp, hin, hout)
+    barrier()
+    e2e_t = time.perf_counter() - te
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+
+    total_pairs = n_pairs * args.steps * world
+    value = total_pairs / elapsed
+    if rank != 0:
+        sp.close()
+        return
+    pk = peaks()
+    clocks = clk.summary()
+    sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    mean_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = 2.0 * n_pairs / mean_launch_s / 1e12
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle as O
+            O.build()
+            c = sharp_coeffs()
+            m64 = m.astype(np.float64)
+            oracle_sample(16, 5, c, info["n_intervals"], m64)
+            p, t = oracle_sample(args.cpu_pixels, 6, c, info["n_intervals"], m64)
+            cpu = {"value": p / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{args.cpu_pixels} random output pixels of the nside-2048 map, "
+                             f"all-pairs FP64 brute force ({t:.1f} s)"}
+        except Exception as e:  # the baseline must not sink the GPU number
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {e}"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_desc({"n_pairs_per_map": n_pairs, "n_intervals": info["n_intervals"],
+                                 "split_fit_s": round(t_split, 2),
+                                 "eq6_frac_error_alpha5": info["frac_error"],
+                                 "parallelism": f"independent maps x{world}"}),
+        "maps_per_s": world * args.steps / elapsed,
+        "roofline": {"bound": "alu", "kernel": "conv_general_kernel",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "note": "2 FLOP (one FMA) per in-disc pixel pair; peak = 152 SMs x 128 "
+                             "FP32 lanes x 2 x max SM clock"},
+        "e2e": {"value": total_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 4 * npix,
+                "d2h_bytes_per_step": 4 * npix},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    sp.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-pixels", type=int, default=512)
+    ap.add_argument("--ref-pixels", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * ksconv.h -- C ABI of libksconv, a GB300 (sm_103a) library for the real-space
+ * half of the kernel-splitting spherical convolution of Sutter, Wandelt &
+ * Elsner, "Using hybrid GPU/CPU kernel splitting to accelerate spherical
+ * convolutions" (arXiv:1409.4441).
+ *
+ * The method (Sec. 2, Fig. 1): a radially symmetric kernel K_l is split into a
+ * band-limited harmonic part Khat_l (l <= l_cut), applied by a spherical-
+ * harmonic transform, and a compact real-space part Khat_theta (theta <=
+ * theta_cut), applied by direct summation on the GPU:
+ *
+ *     out_i = (4 pi / Npix) * sum_{j : theta_ij <= theta_cut} K_r(theta_ij) m_j
+ *
+ * over a HEALPix map in RING order.  This library fits the split (Eq. 1-6),
+ * tabulates K_r on the GPU and performs that sum.  The harmonic half is the
+ * caller's (any SHT library).
+ *
+ * Conventions
+ *   - Angles are radians.  Maps are float32, HEALPix RING order, 12 nside^2
+ *     values.  nside is a power of two, 1 <= nside <= 8192.
+ *   - Legendre convention: K(z) = sum_l (2l+1)/(4 pi) k_l P_l(z) with
+ *     k_l = 2 pi int K(z) P_l(z) dz, so k_0 = 1 is a unit-integral kernel and
+ *     convolution multiplies spherical-harmonic coefficients by k_l.
+ *   - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *     data_ptr()).  `stream` is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  Every ksc_conv_* call is asynchronous on that
+ *     stream unless stated otherwise; the caller owns all map buffers and must
+ *     keep them alive until the stream has passed the call.
+ *   - The library owns a ksc_split and all device memory inside it; release
+ *     it with ksc_free_split.  A split may be used from several streams at
+ *     once (it is read-only after construction) but must not be freed while
+ *     work that uses it is in flight.
+ *   - Every entry point returns a status code (0 = success, < 0 = error) and
+ *     never throws; ksc_last_error() gives a message for the calling thread.
+ */
+#ifndef KSCONV_H
+#define KSCONV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define KSC_OK 0
+#define KSC_ERR_ARG (-1)           /* invalid argument (sizes, nulls, ranges) */
+#define KSC_ERR_NOMEM (-2)         /* host or device allocation failed        */
+#define KSC_ERR_CUDA (-3)          /* a CUDA runtime call failed              */
+#define KSC_ERR_TIMEOUT (-4)       /* a bounded device wait ran out           */
+#define KSC_ERR_DEVICE_BOUNDS (-5) /* a device-side bounds check fired        */
+#define KSC_ERR_SVD (-6)           /* the split's SVD did not converge        */
+#define KSC_ERR_UNSUPPORTED (-7)   /* valid request this build cannot serve   */
+
+/* ---- split construction (Sec. 2, Eq. 1-6) ------------------------------ */
+#define KSC_SPLIT_LSQ 0   /* weighted least-squares split, Eq. 3-5 (default) */
+#define KSC_SPLIT_SHARP 1 /* Khat_l = K_l (l <= l_cut); real part = the rest */
+#define KSC_SPLIT_NONE 2  /* whole kernel in real space, truncated           */
+
+typedef struct ksc_split ksc_split; /* opaque, library-owned */
+
+typedef struct {
+    int mode;          /* KSC_SPLIT_*                                          */
+    int oversample;    /* real-space unknowns: nodes of an oversample*(lmax+1)
+                          point Gauss-Legendre rule inside the cap (z_cut of
+                          Eq. 4); default 2                                    */
+    double svd_rcond;  /* singular values below svd_rcond * max are dropped
+                          (Sec. 2: 1e-6); default 1e-6                          */
+    double alpha;      /* Eq. 6 numerical-error factor; default 5 (Sec. 3)     */
+    int n_intervals;   /* K_r table intervals in the chord d in [0, d_cut];
+                          0 = automatic (about 96 per shortest l_max
+                          wavelength, at most 8192)                             */
+} ksc_split_opts;
+
+/* Fill *opts with the defaults listed above. */
+int ksc_default_opts(ksc_split_opts *opts);
+
+/*
+ * Fit the split of kernel b_l (l = 0..lmax, host array) for maps of the given
+ * nside and build its device table (Sec. 2, Eq. 1-6; Fig. 1 "kernel
+ * splitting").  cl_in (host, lmax+1 values, or NULL for a flat spectrum) is
+ * the input power spectrum weighting Eq. 2; W = diag((2l+1) C_l^in).
+ *   mode LSQ:   minimises Eq. 2 over Khat_l (l <= l_cut) and the z_cut
+ *               real-space unknowns; rows l <= l_cut are fitted exactly by
+ *               Khat_l and the SVD (with the svd_rcond cut) acts on the
+ *               real-space block of rows l > l_cut.
+ *   mode SHARP: Khat_l = b_l for l <= l_cut; real part = sum over l > l_cut.
+ *   mode NONE:  l_cut is ignored (no harmonic part); real part = b_l.
+ * Requires 1 <= lmax <= 16384, 0 <= l_cut < lmax (LSQ/SHARP),
+ * 0 < theta_cut <= pi.  Runs host FP64 code (OpenMP) and one table-building
+ * kernel on the current device; synchronous.  On success *out owns a new split.
+ * Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_SVD, KSC_ERR_CUDA.
+ */
+int ksc_make_split(const double *b_l, int lmax, int nside, int l_cut,
+                   double theta_cut, const double *cl_in,
+                   const ksc_split_opts *opts, ksc_split **out);
+
+/*
+ * Build a split whose real-space part is given directly by its Legendre
+ * coefficients c_l (l = 0..lmax, host): K_r(theta) = sum_l (2l+1)/(4 pi) c_l
+ * P_l(cos theta) for theta <= theta_cut, 0 beyond (the table of Sec. 3,
+ * Fig. 4).  No harmonic part.  Same requirements and errors as above.
+ */
+int ksc_make_split_real(const double *c_l, int lmax, int nside,
+                        double theta_cut, const ksc_split_opts *opts,
+                        ksc_split **out);
+
+typedef struct {
+    int lmax, l_cut, nside, mode, n_intervals, n_unknowns, n_kept;
+    double theta_cut;     /* radians                                          */
+    double chord_cut;     /* 2 sin(theta_cut / 2)                             */
+    double sigma_rms;     /* Eq. 2 of the fitted split                        */
+    double frac_error;    /* Eq. 6 estimate with opts.alpha                   */
+    long long n_pairs;    /* ordered in-disc pixel pairs (one map), or -1     */
+} ksc_split_desc;
+
+/* Describe a split (host struct, filled synchronously). */
+int ksc_split_info(const ksc_split *s, ksc_split_desc *out);
+/* Copy out the harmonic part Khat_l, l = 0..l_cut (host array). */
+int ksc_split_harmonic(const ksc_split *s, double *k_harm);
+/* Copy out the real-space Legendre coefficients c_l, l = 0..lmax (host). */
+int ksc_split_real_coeffs(const ksc_split *s, double *c_l);
+/* Copy out the fitted kernel K~_l = Khat_l + P Khat_theta (Eq. 1), l = 0..lmax. */
+int ksc_split_model(const ksc_split *s, double *k_tilde);
+/* Copy the device table to host: 4 floats (a0..a3) per interval; on interval
+ * k, K(d) = a0 + t(a1 + t(a2 + t a3)), t = d/h - k, h = chord_cut/n_intervals. */
+int ksc_split_table(const ksc_split *s, float *host_coeffs);
+
+/* ---- the real-space convolution (the hot path) ------------------------- */
+/*
+ * out = real-space convolution of `in` with the split's K_r (both device
+ * arrays of 12 nside^2 floats, nside as given to the split; in != out).
+ * Asynchronous on `stream`.  Errors: KSC_ERR_ARG, KSC_ERR_CUDA.
+ */
+int ksc_conv_real(const ksc_split *s, const float *d_in, float *d_out,
+                  void *stream);
+
+/*
+ * Latitude band: write only output rings ring_lo..ring_hi (1-based HEALPix
+ * ring numbers, 1 <= ring_lo <= ring_hi <= 4 nside - 1); other outputs are
+ * untouched.  Reads whatever input rings the band needs (Sec. 4 latitude
+ * bands with theta_cut overlap).  Results are bit-identical to the same rings
+ * of ksc_conv_real.
+ */
+int ksc_conv_real_rings(const ksc_split *s, const float *d_in, float *d_out,
+                        int ring_lo, int ring_hi, void *stream);
+
+/*
+ * n_maps maps sharing one split: d_in and d_out are [n_maps][12 nside^2]
+ * device arrays (map-major).  Asynchronous.
+ */
+int ksc_conv_real_multimap(const ksc_split *s, const float *d_in,
+                           float *d_out, int n_maps, void *stream);
+
+/*
+ * A ragged batch: n independent convolutions (each its own split, hence its
+ * own nside, beam and theta_cut) in one call; splits, d_in and d_out are
+ * host arrays of n entries.  Asynchronous.
+ */
+int ksc_conv_real_batch(const ksc_split *const *splits,
+                        const float *const *d_in, float *const *d_out, int n,
+                        void *stream);
+
+/*
+ * End-to-end convenience: host map in, host map out (12 nside^2 floats each),
+ * through library-owned device buffers and the split's own stream.
+ * Synchronous.  Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_CUDA.
+ */
+int ksc_conv_real_host(const ksc_split *s, const float *h_in, float *h_out);
+
+/* Count ordered in-disc pixel pairs on the device (synchronous); also stored
+ * in the split and reported by ksc_split_info. */
+int ksc_count_pairs(ksc_split *s, long long *n_pairs);
+
+/* Release a split and its device memory (NULL is a no-op). */
+void ksc_free_split(ksc_split *s);
+
+/* Human-readable name of a status code. */
+const char *ksc_status_string(int status);
+/* Message of the last error on the calling thread ("" if none). */
+const char *ksc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSCONV_H */

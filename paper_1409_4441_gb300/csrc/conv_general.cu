@@ -1,0 +1,194 @@
+// Real-space convolution, general ring-pair gather (Sec. 1-2; Fig. 1 GPU half):
+//
+//   out_i = (4 pi / Npix) sum_{j: theta_ij <= theta_cut} K_r(theta_ij) m_j
+//
+// One thread owns one output pixel.  Input rings within theta_cut of the
+// output ring are visited in chunks; per (output ring, input ring) pair the
+// block precomputes in shared memory, in FP64 and rounded once to FP32,
+//   A = (z - z')^2 + (s - s')^2,   B = 4 s s',
+// so that the squared chord of any pixel pair of the two rings is
+//   d^2 = A + B sin^2(dphi / 2)
+// with every term non-negative (no cancellation near theta = 0).  dphi / 2 is
+// N * pi / (2 L L') for the exact integer N = (2k + t) L' - (2k' + t') L
+// (pixel k of a ring of L pixels sits at phi = (2k + t) pi / L), so no pixel
+// coordinate is ever rounded.  sin is its Taylor series to x^13, accurate to
+// FP32 rounding on |x| <= pi/2.  K_r(d) comes from the cubic Hermite table in
+// shared memory; each input ring's FP32 partial sum is folded into the pixel
+// total with Kahan compensation.
+#include "ksc_internal.h"
+
+namespace ksc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRingChunk = 128;
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ float sin_taylor(float x) {
+    const float x2 = x * x;
+    float p = 1.6059043836821613e-10f;       //  1/13!
+    p = fmaf(p, x2, -2.5052108385441720e-08f); // -1/11!
+    p = fmaf(p, x2, 2.7557319223985893e-06f);  //  1/9!
+    p = fmaf(p, x2, -1.9841269841269841e-04f); // -1/7!
+    p = fmaf(p, x2, 8.3333333333333333e-03f);  //  1/5!
+    p = fmaf(p, x2, -1.6666666666666667e-01f); // -1/3!
+    p = fmaf(p, x2, 1.0f);
+    return x * p;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kThreads)
+conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
+                    const float *__restrict__ in, float *__restrict__ out,
+                    long long map_stride, unsigned long long *__restrict__ count) {
+    extern __shared__ float4 s_tab[];
+    __shared__ float sA[kRingChunk], sB[kRingChunk], sC[kRingChunk], sHW[kRingChunk];
+    __shared__ int sL[kRingChunk], sS[kRingChunk], sT[kRingChunk];
+
+    const int tid = threadIdx.x;
+    if (!COUNT)
+        for (int i = tid; i < P.n_int; i += kThreads) s_tab[i] = P.d_tab[i];
+
+    const float *m = in + (long long)blockIdx.y * map_stride;
+    float *o = out + (long long)blockIdx.y * map_stride;
+    unsigned long long cnt = 0;
+
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const DevRing R = P.d_rings[w.ring];
+        const int L = R.len;
+        const int k = w.k0 + tid;
+        const bool active = k < L;
+        const int2 rg = P.d_range[w.ring];
+        float sum = 0.0f, comp = 0.0f;
+
+        for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
+            const int nq = min(kRingChunk, rg.y - q0 + 1);
+            __syncthreads();
+            if (tid < nq) {
+                const DevRing Q = P.d_rings[q0 + tid];
+                const double dz = R.z - Q.z;
+                const double ds = (Q.z - R.z) * (Q.z + R.z) / (R.s + Q.s);  // s - s'
+                const double A = dz * dz + ds * ds;
+                const double ss = R.s * Q.s;
+                float hw;
+                if (A > (double)P.dc2 * (1.0 + 1e-6)) {
+                    hw = -1.0f;  // no pixel of this ring is within theta_cut
+                } else {
+                    const double cdp = (P.cos_cut - R.z * Q.z) / ss;
+                    double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : acos(cdp));
+                    hw = (float)(dphi * Q.len / (2.0 * kPi)) + 1.0f;
+                }
+                sA[tid] = (float)A;
+                sB[tid] = (float)(4.0 * ss);
+                sC[tid] = (float)(kPi / (2.0 * (double)L * (double)Q.len));
+                sHW[tid] = hw;
+                sL[tid] = Q.len;
+                sS[tid] = Q.start;
+                sT[tid] = Q.phase;
+            }
+            __syncthreads();
+            if (!active) continue;
+            for (int qi = 0; qi < nq; ++qi) {
+                const float hw = sHW[qi];
+                if (hw < 0.0f) continue;
+                const int L2 = sL[qi];
+                const long long num = (long long)(2 * k + R.phase) * L2 - (long long)sT[qi] * L;
+                const float kc = (float)num / (float)(2 * L);
+                int klo = (int)floorf(kc - hw), khi = (int)ceilf(kc + hw);
+                if (2.0f * hw + 1.0f >= (float)L2 || khi - klo + 1 >= L2) {
+                    // the window covers the ring: every pixel exactly once,
+                    // centred so that |dphi| <= pi (1 + 2/L2)
+                    klo = (int)floorf(kc) - L2 / 2;
+                    khi = klo + L2 - 1;
+                }
+                int N = (int)(num - 2LL * klo * L);
+                int idx = klo % L2;
+                if (idx < 0) idx += L2;
+                const float A = sA[qi], B = sB[qi], cs = sC[qi];
+                const float *mr = m + sS[qi];
+                float part = 0.0f;
+                for (int kk = klo; kk <= khi; ++kk) {
+                    const float sn = sin_taylor((float)N * cs);
+                    const float d2 = fmaf(B, sn * sn, A);
+                    if (d2 <= P.dc2) {
+                        if (COUNT) {
+                            ++cnt;
+                        } else {
+                            const float u = sqrtf(d2) * P.inv_h;
+                            const int i = min((int)u, P.n_int - 1);
+                            const float f = u - (float)i;
+                            const float4 c = s_tab[i];
+                            const float kv = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+                            part = fmaf(kv, __ldg(mr + idx), part);
+                        }
+                    }
+                    N -= 2 * L;
+                    if (++idx == L2) idx = 0;
+                }
+                // Kahan: fold this ring's partial sum into the total
+                const float y = part - comp;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            }
+        }
+        if (!COUNT && active) o[R.start + k] = sum * P.domega;
+    }
+    if (COUNT) {
+        // block reduction of the pair counts
+        __shared__ unsigned long long s_cnt[kThreads / 32];
+        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+        if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long t = 0;
+            for (int i = 0; i < kThreads / 32; ++i) t += s_cnt[i];
+            atomicAdd(count, t);
+        }
+    }
+}
+
+} // namespace
+
+cudaError_t launch_conv_general(const ConvPlan &p, const WorkItem *d_items, int n_items,
+                                const float *d_in, float *d_out, int n_maps,
+                                long long map_stride, unsigned long long *d_count,
+                                cudaStream_t st) {
+    if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    const bool count = d_count != nullptr;
+    const size_t smem = count ? 0 : sizeof(float4) * (size_t)p.n_int;
+    int per_sm = 0;
+    cudaError_t e;
+    if (count) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_general_kernel<true>,
+                                                          kThreads, smem);
+    } else {
+        e = cudaFuncSetAttribute(conv_general_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_general_kernel<false>,
+                                                          kThreads, smem);
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int blocks = n_sm * per_sm;
+    if (blocks > n_items) blocks = n_items;
+    dim3 grid(blocks, n_maps);
+    if (count)
+        conv_general_kernel<true><<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out,
+                                                               map_stride, d_count);
+    else
+        conv_general_kernel<false><<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out,
+                                                                map_stride, d_count);
+    return cudaGetLastError();
+}
+
+} // namespace ksc

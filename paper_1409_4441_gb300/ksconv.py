@@ -1,0 +1,250 @@
+"""Thin ctypes binding of libksconv (include/ksconv.h): argument marshalling only.
+
+Every computation runs inside the CUDA/C++ library.  If ``libksconv.so`` is
+missing this module raises on import: there is no CPU fallback.  Device arrays
+are torch CUDA tensors (float32, contiguous); streams default to torch's
+current stream.  Angles are radians.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libksconv.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libksconv.so not built ({LIB_PATH}); run paper_1409_4441_gb300/build.py "
+                      "or __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+KSC_OK = 0
+KSC_ERR_ARG = -1
+KSC_ERR_NOMEM = -2
+KSC_ERR_CUDA = -3
+KSC_ERR_TIMEOUT = -4
+KSC_ERR_DEVICE_BOUNDS = -5
+KSC_ERR_SVD = -6
+KSC_ERR_UNSUPPORTED = -7
+MODES = {"lsq": 0, "sharp": 1, "none": 2}
+
+# Every symbol include/ksconv.h declares.
+EXPORTS = [
+    "ksc_default_opts", "ksc_make_split", "ksc_make_split_real", "ksc_split_info",
+    "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
+    "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
+    "ksc_conv_real_host", "ksc_count_pairs", "ksc_free_split", "ksc_status_string",
+    "ksc_last_error",
+]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("oversample", ctypes.c_int),
+                ("svd_rcond", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("n_intervals", ctypes.c_int)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("l_cut", ctypes.c_int), ("nside", ctypes.c_int),
+                ("mode", ctypes.c_int), ("n_intervals", ctypes.c_int),
+                ("n_unknowns", ctypes.c_int), ("n_kept", ctypes.c_int),
+                ("theta_cut", ctypes.c_double), ("chord_cut", ctypes.c_double),
+                ("sigma_rms", ctypes.c_double), ("frac_error", ctypes.c_double),
+                ("n_pairs", ctypes.c_longlong)]
+
+
+_vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_sig = {
+    "ksc_default_opts": [ctypes.POINTER(Opts)],
+    "ksc_make_split": [_vp, _i, _i, _i, _d, _vp, ctypes.POINTER(Opts), ctypes.POINTER(_vp)],
+    "ksc_make_split_real": [_vp, _i, _i, _d, ctypes.POINTER(Opts), ctypes.POINTER(_vp)],
+    "ksc_split_info": [_vp, ctypes.POINTER(Desc)],
+    "ksc_split_harmonic": [_vp, _vp],
+    "ksc_split_real_coeffs": [_vp, _vp],
+    "ksc_split_model": [_vp, _vp],
+    "ksc_split_table": [_vp, _vp],
+    "ksc_conv_real": [_vp, _vp, _vp, _vp],
+    "ksc_conv_real_rings": [_vp, _vp, _vp, _i, _i, _vp],
+    "ksc_conv_real_multimap": [_vp, _vp, _vp, _i, _vp],
+    "ksc_conv_real_batch": [_vp, _vp, _vp, _i, _vp],
+    "ksc_conv_real_host": [_vp, _vp, _vp],
+    "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
+    "ksc_free_split": [_vp],
+    "ksc_status_string": [_i],
+    "ksc_last_error": [],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _i
+_lib.ksc_free_split.restype = None
+_lib.ksc_status_string.restype = ctypes.c_char_p
+_lib.ksc_last_error.restype = ctypes.c_char_p
+
+
+class KsconvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.ksc_last_error().decode()
+        super().__init__(f"{where}: {_lib.ksc_status_string(code).decode()} ({msg})")
+
+
+def _check(rc: int, where: str):
+    if rc != KSC_OK:
+        raise KsconvError(rc, where)
+
+
+def _dptr(t):
+    """Device address of a torch CUDA tensor (float32, contiguous) or an int."""
+    if isinstance(t, int):
+        return t
+    import torch
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _check(_lib.ksc_default_opts(ctypes.byref(o)), "ksc_default_opts")
+    for k, v in kw.items():
+        setattr(o, k, MODES[v] if k == "mode" else v)
+    return o
+
+
+class Split:
+    """Owner of a ksc_split handle (freed on close/garbage collection)."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("split already freed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ksc_free_split(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def make_split(b_l, nside: int, l_cut: int, theta_cut: float, cl_in=None, **opts) -> Split:
+    """ksc_make_split: fit the Sec. 2 split of kernel b_l and build its device table."""
+    b = np.ascontiguousarray(b_l, dtype=np.float64)
+    cl = None if cl_in is None else np.ascontiguousarray(cl_in, dtype=np.float64)
+    o = default_opts(**opts)
+    h = _vp()
+    _check(_lib.ksc_make_split(b.ctypes.data, b.size - 1, nside, l_cut, float(theta_cut),
+                               None if cl is None else cl.ctypes.data, ctypes.byref(o),
+                               ctypes.byref(h)), "ksc_make_split")
+    return Split(h.value)
+
+
+def make_split_real(c_l, nside: int, theta_cut: float, **opts) -> Split:
+    """ksc_make_split_real: real-space part given by its Legendre coefficients."""
+    c = np.ascontiguousarray(c_l, dtype=np.float64)
+    o = default_opts(**opts)
+    h = _vp()
+    _check(_lib.ksc_make_split_real(c.ctypes.data, c.size - 1, nside, float(theta_cut),
+                                    ctypes.byref(o), ctypes.byref(h)), "ksc_make_split_real")
+    return Split(h.value)
+
+
+def split_info(s: Split) -> dict:
+    d = Desc()
+    _check(_lib.ksc_split_info(s.handle, ctypes.byref(d)), "ksc_split_info")
+    return {f: getattr(d, f) for f, _ in Desc._fields_}
+
+
+def split_harmonic(s: Split) -> np.ndarray:
+    info = split_info(s)
+    out = np.zeros(max(info["l_cut"] + 1, 0))
+    if out.size:
+        _check(_lib.ksc_split_harmonic(s.handle, out.ctypes.data), "ksc_split_harmonic")
+    return out
+
+
+def split_real_coeffs(s: Split) -> np.ndarray:
+    out = np.empty(split_info(s)["lmax"] + 1)
+    _check(_lib.ksc_split_real_coeffs(s.handle, out.ctypes.data), "ksc_split_real_coeffs")
+    return out
+
+
+def split_model(s: Split) -> np.ndarray:
+    out = np.empty(split_info(s)["lmax"] + 1)
+    _check(_lib.ksc_split_model(s.handle, out.ctypes.data), "ksc_split_model")
+    return out
+
+
+def split_table(s: Split) -> np.ndarray:
+    out = np.empty((split_info(s)["n_intervals"], 4), dtype=np.float32)
+    _check(_lib.ksc_split_table(s.handle, out.ctypes.data), "ksc_split_table")
+    return out
+
+
+def count_pairs(s: Split) -> int:
+    n = ctypes.c_longlong()
+    _check(_lib.ksc_count_pairs(s.handle, ctypes.byref(n)), "ksc_count_pairs")
+    return n.value
+
+
+def conv_real(s: Split, d_in, d_out, stream=None):
+    _check(_lib.ksc_conv_real(s.handle, _dptr(d_in), _dptr(d_out), _stream(stream)),
+           "ksc_conv_real")
+    return d_out
+
+
+def conv_real_rings(s: Split, d_in, d_out, ring_lo: int, ring_hi: int, stream=None):
+    _check(_lib.ksc_conv_real_rings(s.handle, _dptr(d_in), _dptr(d_out), ring_lo, ring_hi,
+                                    _stream(stream)), "ksc_conv_real_rings")
+    return d_out
+
+
+def conv_real_multimap(s: Split, d_in, d_out, n_maps: int, stream=None):
+    _check(_lib.ksc_conv_real_multimap(s.handle, _dptr(d_in), _dptr(d_out), n_maps,
+                                       _stream(stream)), "ksc_conv_real_multimap")
+    return d_out
+
+
+def conv_real_batch(splits, d_ins, d_outs, stream=None):
+    n = len(splits)
+    hs = (_vp * n)(*[s.handle for s in splits])
+    ins = (_vp * n)(*[_dptr(t) for t in d_ins])
+    outs = (_vp * n)(*[_dptr(t) for t in d_outs])
+    _check(_lib.ksc_conv_real_batch(hs, ins, outs, n, _stream(stream)), "ksc_conv_real_batch")
+    return d_outs
+
+
+def conv_real_host(s: Split, h_in, h_out=None):
+    """Host float32 map in, host float32 map out (synchronous)."""
+    if isinstance(h_in, np.ndarray):
+        hi = np.ascontiguousarray(h_in, dtype=np.float32)
+        ho = np.empty_like(hi) if h_out is None else h_out
+        _check(_lib.ksc_conv_real_host(s.handle, hi.ctypes.data, ho.ctypes.data),
+               "ksc_conv_real_host")
+        return ho
+    # pinned torch CPU tensors
+    ho = h_out
+    _check(_lib.ksc_conv_real_host(s.handle, h_in.data_ptr(), ho.data_ptr()),
+           "ksc_conv_real_host")
+    return ho

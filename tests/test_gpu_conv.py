@@ -1,0 +1,191 @@
+"""GPU parity of the real-space convolution (the hot path) against the FP64 oracle.
+
+Tolerance (per output pixel): |gpu - oracle| <= 1e-6 * rms(oracle) + ambig, where
+ambig bounds pairs whose chord^2 lies within 1e-6 (relative) of the cut, which
+FP32 and FP64 may legitimately classify differently.  Maps are rounded to FP32
+before both sides see them.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1409_4441_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ARC = inputs.ARCMIN
+
+
+@pytest.fixture(scope="module")
+def K():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1409_4441_gb300 import ksconv
+    assert torch.cuda.is_available()
+    return ksconv
+
+
+def _run(K, sp, m32):
+    x = torch.tensor(m32, device="cuda")
+    y = torch.full_like(x, float("nan"))
+    K.conv_real(sp, x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def _check(got, ref, amb, rel=1e-6):
+    rms = np.sqrt(np.mean(ref ** 2))
+    err = np.abs(got - ref)
+    bad = err > rel * rms + amb
+    assert not np.any(np.isnan(got))
+    assert not bad.any(), (f"{bad.sum()} pixels over tolerance; max err {err.max():.3e}, "
+                           f"rms {rms:.3e}")
+    return err.max() / rms
+
+
+def test_table_matches_oracle_legendre_sum(K):
+    lmax, nside = 1535, 512
+    tc = 90 * ARC
+    c = inputs.gaussian_beam(lmax, 20 * ARC)
+    c[:257] = 0.0
+    with K.make_split_real(c, nside, tc) as sp:
+        info = K.split_info(sp)
+        tab = K.split_table(sp).astype(np.float64)
+    n_int = info["n_intervals"]
+    dc = O.chord_cut(tc)
+    assert info["chord_cut"] == pytest.approx(dc, rel=1e-15)
+    d = np.random.default_rng(3).uniform(0, dc, 50000)
+    h = dc / n_int
+    k = np.minimum((d / h).astype(int), n_int - 1)
+    t = d / h - k
+    a = tab[k]
+    lib = a[:, 0] + t * (a[:, 1] + t * (a[:, 2] + t * a[:, 3]))
+    tK, tD = O.hermite_nodes(c, tc, n_int)
+    orc = O.hermite_eval(tK, tD, tc, d)
+    exact = O.legendre_sum(c, 1 - d * d / 2)
+    peak = np.abs(exact).max()
+    assert np.abs(lib - orc).max() <= 2e-7 * peak
+    assert np.abs(lib - exact).max() <= 3e-7 * peak
+
+
+@pytest.mark.parametrize("nside,tc_deg,lmax,fwhm_deg", [
+    (1, 60.0, 3, 40.0),      # twelve pixels, several per disc
+    (8, 180.0, 23, 10.0),    # whole sphere: every input ring, full-ring windows
+    (16, 20.0, 47, 6.0),     # caps and belt, ragged 256-pixel chunks
+    (32, 0.5, 95, 3.0),      # disc smaller than a pixel: only the self pair
+    (64, 6.0, 191, 2.0),     # the 2-degree nside-64 workload (3 x FWHM cut)
+])
+def test_full_map_parity(K, nside, tc_deg, lmax, fwhm_deg):
+    tc = np.radians(tc_deg)
+    c = inputs.gaussian_beam(lmax, np.radians(fwhm_deg))
+    m = inputs.white_noise_map(nside, inputs.seed_for(1, nside)).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as sp:
+        n_int = K.split_info(sp)["n_intervals"]
+        got = _run(K, sp, m)
+    ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int))
+    _check(got, ref, amb)
+    # against the exact kernel too (table interpolation error included)
+    ex, amb2 = O.brute_conv(nside, m.astype(np.float64), tc, c=c)
+    _check(got, ex, amb2, rel=2e-6)
+
+
+def test_self_pair_only(K):
+    nside = 32
+    tc = np.radians(0.5)
+    c = inputs.gaussian_beam(95, np.radians(3.0))
+    m = inputs.white_noise_map(nside, 99).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as sp:
+        got = _run(K, sp, m)
+        tab = K.split_table(sp)
+    k0 = float(tab[0, 0])
+    np.testing.assert_allclose(got, m * k0 * np.float32(4 * np.pi / O.npix(nside)), rtol=1e-6)
+
+
+def test_high_pass_kernel_parity_nside256(K):
+    """An oscillating real-space remainder (l > l_cut of a beam) at 256-pixel chunks
+    over many rings, full map against the tabulated-kernel oracle."""
+    nside, lmax, lcut = 128, 383, 64
+    tc = np.radians(4.0)
+    c = inputs.gaussian_beam(lmax, np.radians(1.0))
+    c[: lcut + 1] = 0.0
+    m = inputs.white_noise_map(nside, 5).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as sp:
+        n_int = K.split_info(sp)["n_intervals"]
+        got = _run(K, sp, m)
+    pix = inputs.sample_pixels(nside, 3000, 17)
+    ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int),
+                            out_pix=pix)
+    _check(got[pix], ref, amb)
+
+
+@pytest.mark.parametrize("tc_arcmin", [240.0])
+def test_nside2048_sampled_parity(K, tc_arcmin):
+    """The Planck-resolution workload (nside 2048, l_max 4096, 5' beam high-passed at
+    l_cut 1024, theta_cut 240'), same launch as the benchmark, checked on sampled
+    output pixels."""
+    nside, lmax, lcut = 2048, 4096, 1024
+    tc = tc_arcmin * ARC
+    c = inputs.gaussian_beam(lmax, 5 * ARC)
+    c[: lcut + 1] = 0.0
+    m = inputs.white_noise_map(nside, inputs.seed_for(3)).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as sp:
+        n_int = K.split_info(sp)["n_intervals"]
+        got = _run(K, sp, m)
+    pix = inputs.sample_pixels(nside, 200, 23)
+    ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int),
+                            out_pix=pix)
+    _check(got[pix], ref, amb)
+
+
+def test_bands_multimap_batch_and_host_are_bitwise(K):
+    nside = 32
+    tc = np.radians(8.0)
+    c = inputs.gaussian_beam(95, np.radians(3.0))
+    maps = np.stack([inputs.white_noise_map(nside, 40 + i) for i in range(3)]).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as sp:
+        x = torch.tensor(maps, device="cuda")
+        full = torch.empty_like(x)
+        for i in range(3):
+            K.conv_real(sp, x[i], full[i])
+        # latitude bands, written into one output in several calls
+        band = torch.full_like(x[0], float("nan"))
+        nr = 4 * nside - 1
+        for lo, hi in [(1, 17), (18, 64), (65, nr)]:
+            K.conv_real_rings(sp, x[0], band, lo, hi)
+        mm = torch.empty_like(x)
+        K.conv_real_multimap(sp, x, mm, 3)
+        torch.cuda.synchronize()
+        host = K.conv_real_host(sp, maps[1])
+        assert torch.equal(band, full[0])
+        assert torch.equal(mm, full)
+        assert np.array_equal(host, full[1].cpu().numpy())
+    # ragged batch of different nsides / kernels
+    specs = [(8, 20.0, 23, 8.0), (16, 12.0, 47, 4.0), (32, 8.0, 95, 3.0)]
+    sps, ins, outs, singles = [], [], [], []
+    for ns, td, lm, fw in specs:
+        cc = inputs.gaussian_beam(lm, np.radians(fw))
+        sps.append(K.make_split_real(cc, ns, np.radians(td)))
+        ins.append(torch.tensor(inputs.white_noise_map(ns, ns).astype(np.float32), device="cuda"))
+        outs.append(torch.empty_like(ins[-1]))
+        singles.append(torch.empty_like(ins[-1]))
+        K.conv_real(sps[-1], ins[-1], singles[-1])
+    K.conv_real_batch(sps, ins, outs)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, singles):
+        assert torch.equal(a, b)
+    for s in sps:
+        s.close()
+
+
+def test_pair_count_matches_oracle(K):
+    nside = 32
+    tc = np.radians(7.3)
+    c = inputs.gaussian_beam(95, np.radians(3.0))
+    with K.make_split_real(c, nside, tc) as sp:
+        n = K.count_pairs(sp)
+        assert K.split_info(sp)["n_pairs"] == n
+    cnt = O.count_pairs(nside, tc)
+    _, amb = O.brute_conv(nside, np.ones(O.npix(nside)), tc, c=np.array([4 * np.pi]), amb_eps=1e-6)
+    n_amb = int(round(amb.sum() / (4 * np.pi / O.npix(nside))))
+    assert abs(n - cnt.sum()) <= n_amb
