@@ -22,8 +22,9 @@
  *     k_l = 2 pi int K(z) P_l(z) dz, so k_0 = 1 is a unit-integral kernel and
  *     convolution multiplies spherical-harmonic coefficients by k_l.
  *   - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
- *     data_ptr()).  `stream` is a cudaStream_t passed as void* (NULL = the
- *     legacy default stream).  Every ksc_conv_* call is asynchronous on that
+ *     data_ptr()), 16-byte aligned (map data is staged by bulk async copies;
+ *     misaligned maps are rejected with KSC_ERR_ARG).  `stream` is a
+ *     cudaStream_t passed as void* (NULL = the legacy default stream).  Every ksc_conv_* call is asynchronous on that
  *     stream unless stated otherwise; the caller owns all map buffers and must
  *     keep them alive until the stream has passed the call.
  *   - The library owns a ksc_split and all device memory inside it; release
@@ -68,6 +69,8 @@ typedef struct {
     int n_intervals;   /* K_r table intervals in the chord d in [0, d_cut];
                           0 = automatic (about 96 per shortest l_max
                           wavelength, at most 8192)                             */
+    int path;          /* 0 (default): circulant belt kernel + symmetric gather;
+                          1: general ring-pair gather only (reference path)   */
 } ksc_split_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -110,6 +113,8 @@ typedef struct {
     double sigma_rms;     /* Eq. 2 of the fitted split                        */
     double frac_error;    /* Eq. 6 estimate with opts.alpha                   */
     long long n_pairs;    /* ordered in-disc pixel pairs (one map), or -1     */
+    long long n_pairs_belt; /* of which both pixels lie in the belt, or -1    */
+    int path;             /* kernel path in use (see ksc_split_opts.path)     */
 } ksc_split_desc;
 
 /* Describe a split (host struct, filled synchronously). */
@@ -166,9 +171,28 @@ int ksc_conv_real_batch(const ksc_split *const *splits,
  */
 int ksc_conv_real_host(const ksc_split *s, const float *h_in, float *h_out);
 
+/*
+ * One stage of ksc_conv_real, for profiling and custom scheduling: stage 1 =
+ * the circulant kernel for belt-belt ring pairs (writes the belt outputs; a
+ * no-op on path 1), stage 2 = the gather for every other pair (writes cap
+ * outputs and, after stage 1, adds the cap inputs of belt outputs).  Stage 1
+ * then stage 2 on one stream equals ksc_conv_real bit for bit.
+ */
+int ksc_conv_real_stage(const ksc_split *s, const float *d_in, float *d_out,
+                        int stage, void *stream);
+
 /* Count ordered in-disc pixel pairs on the device (synchronous); also stored
- * in the split and reported by ksc_split_info. */
+ * in the split (with the belt-belt subset) and reported by ksc_split_info. */
 int ksc_count_pairs(ksc_split *s, long long *n_pairs);
+
+/*
+ * Synchronize `stream` and report device-side errors raised by earlier calls
+ * on this split: KSC_ERR_TIMEOUT when a bounded wait inside a kernel ran out
+ * (the kernel stopped early and its output is incomplete),
+ * KSC_ERR_DEVICE_BOUNDS when a device-side bounds check fired.  Clears the
+ * flag.  KSC_OK otherwise.
+ */
+int ksc_device_status(const ksc_split *s, void *stream);
 
 /* Release a split and its device memory (NULL is a no-op). */
 void ksc_free_split(ksc_split *s);

@@ -1,5 +1,6 @@
 // C ABI of libksconv (declared in include/ksconv.h).
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -41,6 +42,9 @@ void release(ksc_split *s) {
     cudaFree(s->d_rings);
     cudaFree(s->d_range);
     cudaFree(s->d_items);
+    cudaFree(s->d_items_sym);
+    cudaFree(s->d_items_belt);
+    cudaFree(s->d_err);
     cudaFree(s->d_io);
     if (s->own_stream) cudaStreamDestroy(s->own_stream);
     delete s;
@@ -80,15 +84,63 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         int hi = (int)(std::upper_bound(th.begin(), th.end(), th[r] + tc) - th.begin()) - 1;
         range[r] = make_int2(std::max(lo, 0), std::min(hi, nr - 1));
     }
-    // Work list: 256-pixel chunks of every ring, ring by ring.
-    std::vector<ksc::WorkItem> items;
+    // Work lists (ring by ring, with per-ring prefixes for latitude bands):
+    //  - all:  256-pixel chunks of every ring (pair counting, fallback);
+    //  - belt: belt_chunk()-pixel chunks of belt rings (circulant kernel);
+    //  - sym:  first-quarter chunks of northern rings (and the equator) for the
+    //          symmetric gather: cap rings, plus belt rings that reach a cap
+    //          (every northern ring when the belt kernel is not used).
+    const int belt_lo = nside - 1, belt_hi = 3 * nside - 1, eq = 2 * nside - 1;
+    std::vector<ksc::WorkItem> items, items_sym;
+    std::vector<int2> items_belt;
     s->ring_first_item.assign(nr + 1, 0);
+    s->ring_first_sym.assign(nr + 1, 0);
+    s->ring_first_belt.assign(nr + 1, 0);
+    const int bc = ksc::belt_chunk();
+    int max_nd = 0;
     for (int r = 0; r < nr; ++r) {
         s->ring_first_item[r] = (int)items.size();
+        s->ring_first_sym[r] = (int)items_sym.size();
+        s->ring_first_belt[r] = (int)items_belt.size();
         for (int k0 = 0; k0 < g.len[r]; k0 += 256) items.push_back({r, k0});
+        const bool belt = r >= belt_lo && r <= belt_hi;
+        const bool reaches_cap = range[r].x < belt_lo || range[r].y > belt_hi;
+        if (r <= eq && (!belt || reaches_cap || o.path == 1))
+            for (int k0 = 0; k0 < g.len[r] / 4; k0 += ksc::sym_chunk()) items_sym.push_back({r, k0});
+        if (belt) {
+            for (int k0 = 0; k0 < g.len[r]; k0 += bc) items_belt.push_back(make_int2(r, k0));
+            // widest circulant window of this ring (same arithmetic as the kernel)
+            const int L = g.len[r];
+            for (int q = std::max(range[r].x, belt_lo); q <= std::min(range[r].y, belt_hi); ++q) {
+                double ss = g.s[r] * g.s[q];
+                double cdp = (1.0 - 0.5 * s->chord_cut * s->chord_cut - g.z[r] * g.z[q]) / ss;
+                double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : std::acos(cdp));
+                int w = (int)std::ceil(dphi * L / (2.0 * kPi)) + 1;
+                int n = std::min(2 * w + 1, L);
+                max_nd = std::max(max_nd, n);
+            }
+        }
     }
     s->ring_first_item[nr] = (int)items.size();
+    s->ring_first_sym[nr] = (int)items_sym.size();
+    s->ring_first_belt[nr] = (int)items_belt.size();
     s->n_items = (int)items.size();
+    s->n_items_sym = (int)items_sym.size();
+    s->n_items_belt = (int)items_belt.size();
+    // shared-memory segment: chunk + padded window + alignment, with slack for
+    // rounding differences between host and device acos
+    const int seg = bc + max_nd + 6 * 13 + 16;
+    s->seg_cap = (seg + 3) & ~3;
+    const bool belt_ok = s->n_items_belt > 0 && 12ull * s->seg_cap <= 200ull * 1024;
+    s->path = o.path;
+    if (!belt_ok && o.path == 0) {
+        // belt windows too wide for shared memory: the general gather does it all
+        s->path = 1;
+    }
+    if (s->path == 1) {
+        s->n_items_belt = 0;
+        s->seg_cap = 0;
+    }
 
     cudaError_t e;
     cudaGetDevice(&s->device);
@@ -98,6 +150,14 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         return cuda_fail(e, "upload ring ranges");
     if ((e = dev_upload(&s->d_items, items.data(), items.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
+    if ((e = dev_upload(&s->d_items_sym, items_sym.data(), items_sym.size())) != cudaSuccess)
+        return cuda_fail(e, "upload work list");
+    if ((e = dev_upload(&s->d_items_belt, items_belt.data(), items_belt.size())) != cudaSuccess)
+        return cuda_fail(e, "upload work list");
+    if ((e = cudaMalloc(&s->d_err, sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "error flag");
+    if ((e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess)
+        return cuda_fail(e, "error flag");
 
     // Table build on the GPU: FP64 Legendre recurrence per node (csrc/table.cu).
     double *d_c = nullptr, *d_nodes = nullptr;
@@ -128,8 +188,12 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     p.n_int = n_int;
     p.inv_h = (float)(n_int / s->chord_cut);
     p.dc2 = (float)(s->chord_cut * s->chord_cut);
+    // theta_cut = pi: every pair, whatever the FP32 rounding of antipodal chords
+    if (s->theta_cut >= kPi) p.dc2 = 5.0f;
     p.cos_cut = 1.0 - 0.5 * s->chord_cut * s->chord_cut;
     p.domega = (float)(4.0 * kPi / (double)p.npix);
+    p.belt_lo = belt_lo;
+    p.belt_hi = belt_hi;
     return KSC_OK;
 }
 
@@ -148,6 +212,7 @@ ksc_split_opts resolve_opts(const ksc_split_opts *opts) {
         if (o.oversample <= 0) o.oversample = 2;
         if (!(o.svd_rcond > 0.0)) o.svd_rcond = 1e-6;
         if (!(o.alpha > 0.0)) o.alpha = 5.0;
+        if (o.path != 1) o.path = 0;
     }
     return o;
 }
@@ -156,6 +221,41 @@ int check_maps(const ksc_split *s, const void *a, const void *b) {
     if (!s) return fail(KSC_ERR_ARG, "null split");
     if (!a || !b) return fail(KSC_ERR_ARG, "null map pointer");
     if (a == b) return fail(KSC_ERR_ARG, "in and out must be different buffers");
+    if (((uintptr_t)a | (uintptr_t)b) & 15u)
+        return fail(KSC_ERR_ARG, "maps must be 16-byte aligned");
+    return KSC_OK;
+}
+
+// The real-space convolution of output rings [r0, r1] (0-based, inclusive).
+// Default path: circulant belt kernel first (writes belt outputs), then the
+// symmetric gather (writes cap outputs, adds cap inputs to belt outputs).
+// path 1: the general gather alone.
+int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
+                long long stride, int r0, int r1, cudaStream_t st) {
+    cudaError_t e;
+    if (s->path == 1) {
+        const int c = s->ring_first_item[r0], d = s->ring_first_item[r1 + 1];
+        e = ksc::launch_conv_general(s->plan, s->d_items + c, d - c, d_in, d_out, n_maps,
+                                     stride, 0, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
+        return KSC_OK;
+    }
+    const int a = s->ring_first_belt[r0], b = s->ring_first_belt[r1 + 1];
+    e = ksc::launch_conv_belt(s->plan, s->d_items_belt + a, b - a, s->seg_cap, d_in, d_out,
+                              n_maps, stride, s->d_err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "belt kernel launch");
+    // northern rings r whose own or mirror ring (nr - 1 - r) lies in the band
+    const int nr = s->plan.nrings, eq = (nr - 1) / 2;
+    int lo = nr, hi = -1;
+    if (r0 <= eq) { lo = r0; hi = std::min(r1, eq); }                // own ring in band
+    const int m0 = std::max(0, nr - 1 - r1), m1 = std::min(nr - 1 - r0, eq);
+    if (m0 <= m1) { lo = std::min(lo, m0); hi = std::max(hi, m1); }  // mirror in band
+    if (lo <= hi) {
+        const int c = s->ring_first_sym[lo], d = s->ring_first_sym[hi + 1];
+        e = ksc::launch_conv_sym(s->plan, s->d_items_sym + c, d - c, d_in, d_out, n_maps, stride,
+                                 s->n_items_belt > 0 ? 1 : 0, r0, r1, st);
+        if (e != cudaSuccess) return cuda_fail(e, "symmetric kernel launch");
+    }
     return KSC_OK;
 }
 
@@ -170,6 +270,7 @@ int ksc_default_opts(ksc_split_opts *opts) {
     opts->svd_rcond = 1e-6;
     opts->alpha = 5.0;
     opts->n_intervals = 0;
+    opts->path = 0;
     return KSC_OK;
 }
 
@@ -248,6 +349,7 @@ int ksc_split_info(const ksc_split *s, ksc_split_desc *d) {
     d->n_intervals = s->n_int; d->n_unknowns = s->n_unknowns; d->n_kept = s->n_kept;
     d->theta_cut = s->theta_cut; d->chord_cut = s->chord_cut;
     d->sigma_rms = s->sigma_rms; d->frac_error = s->frac_error; d->n_pairs = s->n_pairs;
+    d->n_pairs_belt = s->n_pairs_belt; d->path = s->path;
     return KSC_OK;
 }
 
@@ -279,10 +381,7 @@ int ksc_split_table(const ksc_split *s, float *h) {
 int ksc_conv_real(const ksc_split *s, const float *d_in, float *d_out, void *stream) {
     int rc = check_maps(s, d_in, d_out);
     if (rc) return rc;
-    cudaError_t e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, 1,
-                                             0, nullptr, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "conv launch");
-    return KSC_OK;
+    return launch_conv(s, d_in, d_out, 1, 0, 0, s->plan.nrings - 1, (cudaStream_t)stream);
 }
 
 int ksc_conv_real_rings(const ksc_split *s, const float *d_in, float *d_out, int ring_lo,
@@ -292,11 +391,7 @@ int ksc_conv_real_rings(const ksc_split *s, const float *d_in, float *d_out, int
     const int nr = 4 * s->nside - 1;
     if (ring_lo < 1 || ring_hi > nr || ring_lo > ring_hi)
         return fail(KSC_ERR_ARG, "ring range outside 1..4 nside - 1");
-    const int a = s->ring_first_item[ring_lo - 1], b = s->ring_first_item[ring_hi];
-    cudaError_t e = ksc::launch_conv_general(s->plan, s->d_items + a, b - a, d_in, d_out, 1, 0,
-                                             nullptr, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "conv launch");
-    return KSC_OK;
+    return launch_conv(s, d_in, d_out, 1, 0, ring_lo - 1, ring_hi - 1, (cudaStream_t)stream);
 }
 
 int ksc_conv_real_multimap(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
@@ -304,11 +399,8 @@ int ksc_conv_real_multimap(const ksc_split *s, const float *d_in, float *d_out, 
     int rc = check_maps(s, d_in, d_out);
     if (rc) return rc;
     if (n_maps < 1 || n_maps > 65535) return fail(KSC_ERR_ARG, "n_maps outside 1..65535");
-    cudaError_t e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out,
-                                             n_maps, s->plan.npix, nullptr,
-                                             (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "conv launch");
-    return KSC_OK;
+    return launch_conv(s, d_in, d_out, n_maps, s->plan.npix, 0, s->plan.nrings - 1,
+                       (cudaStream_t)stream);
 }
 
 int ksc_conv_real_batch(const ksc_split *const *splits, const float *const *d_in,
@@ -342,30 +434,70 @@ int ksc_conv_real_host(const ksc_split *cs, const float *h_in, float *h_out) {
     float *din = s->d_io, *dout = s->d_io + s->plan.npix;
     if ((e = cudaMemcpyAsync(din, h_in, bytes, cudaMemcpyHostToDevice, s->own_stream)) != cudaSuccess)
         return cuda_fail(e, "host to device copy");
-    e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, din, dout, 1, 0, nullptr,
-                                 s->own_stream);
-    if (e != cudaSuccess) return cuda_fail(e, "conv launch");
+    int rc = launch_conv(s, din, dout, 1, 0, 0, s->plan.nrings - 1, s->own_stream);
+    if (rc) return rc;
     if ((e = cudaMemcpyAsync(h_out, dout, bytes, cudaMemcpyDeviceToHost, s->own_stream)) != cudaSuccess)
         return cuda_fail(e, "device to host copy");
     if ((e = cudaStreamSynchronize(s->own_stream)) != cudaSuccess)
         return cuda_fail(e, "host path synchronize");
+    return ksc_device_status(s, s->own_stream);
+}
+
+int ksc_device_status(const ksc_split *s, void *stream) {
+    if (!s) return fail(KSC_ERR_ARG, "null split");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "error flag read");
+    if (flag != 0) {
+        cudaMemset(s->d_err, 0, sizeof(int));
+        return fail(flag, "a device-side check fired during an earlier call");
+    }
     return KSC_OK;
 }
 
 int ksc_count_pairs(ksc_split *s, long long *n_pairs) {
     if (!s || !n_pairs) return fail(KSC_ERR_ARG, "null argument");
     unsigned long long *d_cnt = nullptr;
-    cudaError_t e = cudaMalloc(&d_cnt, sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&d_cnt, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(e, "count buffer");
-    cudaMemset(d_cnt, 0, sizeof(unsigned long long));
-    e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, nullptr, nullptr, 1, 0, d_cnt,
-                                 0);
-    unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaMemset(d_cnt, 0, 2 * sizeof(unsigned long long));
+    e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, nullptr, nullptr, 1, 0, 0,
+                                 d_cnt, 0);
+    if (e == cudaSuccess)
+        e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, nullptr, nullptr, 1, 0, 1,
+                                     d_cnt + 1, 0);
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost);
     cudaFree(d_cnt);
     if (e != cudaSuccess) return cuda_fail(e, "pair count");
-    s->n_pairs = (long long)h;
+    s->n_pairs = (long long)h[0];
+    s->n_pairs_belt = (long long)h[1];
     *n_pairs = s->n_pairs;
+    return KSC_OK;
+}
+
+int ksc_conv_real_stage(const ksc_split *s, const float *d_in, float *d_out, int stage,
+                        void *stream) {
+    int rc = check_maps(s, d_in, d_out);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (stage == 1) {
+        e = ksc::launch_conv_belt(s->plan, s->d_items_belt, s->n_items_belt, s->seg_cap, d_in,
+                                  d_out, 1, 0, s->d_err, st);
+    } else if (stage == 2) {
+        if (s->path == 1)
+            e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, 1, 0, 0,
+                                         nullptr, st);
+        else
+            e = ksc::launch_conv_sym(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out, 1, 0,
+                                     s->n_items_belt > 0 ? 1 : 0, 0, s->plan.nrings - 1, st);
+    } else {
+        return fail(KSC_ERR_ARG, "stage must be 1 or 2");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "stage launch");
     return KSC_OK;
 }
 

@@ -1,0 +1,312 @@
+// Real-space convolution, equatorial-belt ring pairs (circulant form).
+//
+// In the HEALPix belt (|z| <= 2/3) every ring has L = 4 nside pixels.  For an
+// output ring and an input ring of the belt, pixel k of the first and k' of
+// the second are dphi apart with dphi/2 = (t - t' - 2 (k' - k)) pi / (2L), so
+// the kernel weight depends on Delta = k' - k only:
+//
+//   out_r[k] += sum_Delta w_{r r'}[Delta] * m_{r'}[(k + Delta) mod L]
+//
+// (a circular correlation).  Each CTA owns a chunk of C = kU * kThreads
+// consecutive output pixels of one belt ring and walks the belt input rings
+// within theta_cut.  Per input ring it
+//   1. issues 1-D TMA bulk copies (cp.async.bulk, mbarrier completion) of the
+//      input segment m_{r'}[k0 + Delta_0 .. k0 + Delta_0 + C + nD - 1] (wrapped
+//      round the ring) into the other shared-memory buffer, ahead of use;
+//   2. computes the weight vector w[Delta] (chord^2 = A + B sin^2(dphi/2) from
+//      FP64 ring constants, cubic Hermite table, zero outside the cut);
+//   3. runs the FFMA sliding window: each thread keeps kU consecutive outputs
+//      in registers; a block of kU weights and 2kU-1 inputs gives kU*kU FFMAs
+//      for 2kU shared-memory loads.  kU is odd, so the kU-word stride between
+//      lanes hits 32 distinct banks.
+//   4. folds the FP32 ring partial sums into the totals with Kahan steps.
+// Every mbarrier wait is bounded; a wait that runs out raises a device error
+// flag and the kernel stops work instead of hanging.
+#include <cstdint>
+
+#include "ksc_internal.h"
+
+namespace ksc {
+namespace {
+
+constexpr int kU = 13;          // outputs per thread (odd: conflict-free strides)
+constexpr int kThreads = 160;   // 5 warps
+constexpr int kChunk = kU * kThreads;
+constexpr int kMaxWait = 1 << 22;   // mbarrier polls before giving up
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ float sin_taylor(float x) {
+    const float x2 = x * x;
+    float p = 1.6059043836821613e-10f;
+    p = fmaf(p, x2, -2.5052108385441720e-08f);
+    p = fmaf(p, x2, 2.7557319223985893e-06f);
+    p = fmaf(p, x2, -1.9841269841269841e-04f);
+    p = fmaf(p, x2, 8.3333333333333333e-03f);
+    p = fmaf(p, x2, -1.6666666666666667e-01f);
+    p = fmaf(p, x2, 1.0f);
+    return x * p;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for the given phase parity; returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < kMaxWait; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+struct PairGeom {
+    float A, B, cs;     // chord^2 = A + B sin^2(x), x = (t - t' - 2 Delta) * cs
+    int d0;             // first Delta of the padded window
+    int nd;             // padded window length (multiple of 2 kU)
+    int exact_lo, exact_hi;  // Delta range that may carry weight (at most L values)
+    int tdiff;          // t - t'
+    bool empty;
+};
+
+__device__ PairGeom pair_geom(const DevRing &R, const DevRing &Q, double cos_cut, float dc2) {
+    PairGeom g;
+    const int L = R.len;
+    const double dz = R.z - Q.z;
+    const double ds = (Q.z - R.z) * (Q.z + R.z) / (R.s + Q.s);
+    const double A = dz * dz + ds * ds;
+    const double ss = R.s * Q.s;
+    g.A = (float)A;
+    g.B = (float)(4.0 * ss);
+    g.cs = (float)(kPi / (2.0 * L));
+    g.tdiff = R.phase - Q.phase;
+    g.empty = A > (double)dc2 * (1.0 + 1e-6);
+    double cdp = (cos_cut - R.z * Q.z) / ss;
+    double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : acos(cdp));
+    // |dphi| = |t - t' - 2 Delta| pi / L <= dphi_max  (plus one pixel of margin)
+    int w = (int)ceil(dphi * L / (2.0 * kPi)) + 1;
+    int lo = -w, hi = w;
+    if (hi - lo + 1 >= L) {  // whole ring: each input pixel exactly once
+        lo = -(L / 2);
+        hi = lo + L - 1;
+    }
+    g.exact_lo = lo;
+    g.exact_hi = hi;
+    const int n = hi - lo + 1;
+    g.d0 = lo;
+    g.nd = ((n + 2 * kU - 1) / (2 * kU)) * (2 * kU);
+    return g;
+}
+
+__global__ void __launch_bounds__(kThreads)
+conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
+                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
+                 int seg_cap, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *seg0 = reinterpret_cast<float *>(smem_raw);
+    float *seg1 = seg0 + seg_cap;
+    float *wbuf = seg1 + seg_cap;  // seg_cap floats as well
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ PairGeom s_g[2];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const float *m = in + (long long)blockIdx.y * map_stride;
+    float *o = out + (long long)blockIdx.y * map_stride;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase0 = 0u, phase1 = 0u;  // expected parity of bar[0], bar[1]
+
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int r = items[it].x, k0 = items[it].y;
+        const DevRing R = P.d_rings[r];
+        const int L = R.len;
+        const int2 rg = P.d_range[r];
+        const int q_lo = max(rg.x, P.belt_lo), q_hi = min(rg.y, P.belt_hi);
+        const int kb = tid * kU;  // first output (chunk-relative) of this thread
+        float sum[kU], comp[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) sum[u] = comp[u] = 0.0f;
+
+        // issue the copy of input ring q into buffer b
+        auto issue = [&](int q, int b) {
+            const DevRing Q = P.d_rings[q];
+            PairGeom g = pair_geom(R, Q, P.cos_cut, P.dc2);
+            s_g[b] = g;
+            if (g.empty) return;
+            // ring coordinates [a, a + n), a aligned down to 4 floats
+            int a = k0 + g.d0;
+            int n = kChunk + g.nd - 1;
+            int a4 = a & ~3;       // floor to a multiple of 4 (also for negatives)
+            n += a - a4;
+            n = (n + 3) & ~3;
+            if (n > seg_cap) {  // never expected: the host sized seg_cap for every pair
+                atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
+                s_g[b].empty = true;
+                return;
+            }
+            float *dst = b ? seg1 : seg0;
+            const float *ring = m + Q.start;
+            uint32_t total = 4u * (uint32_t)n;
+            mbar_expect_tx(&bar[b], total);
+            int pos = a4, done = 0;
+            while (done < n) {
+                int pm = ((pos % L) + L) % L;
+                int len = min(n - done, L - pm);
+                bulk_g2s(dst + done, ring + pm, 4u * (uint32_t)len, &bar[b]);
+                done += len;
+                pos += len;
+            }
+        };
+
+        if (tid == 0 && q_lo <= q_hi) issue(q_lo, 0);
+        int b = 0;
+        for (int q = q_lo; q <= q_hi; ++q, b ^= 1) {
+            __syncthreads();  // previous pair's buffers are free; s_g[b] visible
+            if (tid == 0 && q + 1 <= q_hi) issue(q + 1, b ^ 1);
+            const PairGeom g = s_g[b];
+            if (g.empty) continue;
+            // weights for this ring pair (zero outside the cut / exact window)
+            for (int j = tid; j < g.nd; j += kThreads) {
+                const int D = g.d0 + j;
+                float wv = 0.0f;
+                if (D >= g.exact_lo && D <= g.exact_hi) {
+                    const float sn = sin_taylor((float)(g.tdiff - 2 * D) * g.cs);
+                    const float d2 = fmaf(g.B, sn * sn, g.A);
+                    if (d2 <= P.dc2) {
+                        const float uu = sqrtf(d2) * P.inv_h;
+                        const int i = min((int)uu, P.n_int - 1);
+                        const float f = uu - (float)i;
+                        const float4 c = __ldg(&P.d_tab[i]);
+                        wv = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+                    }
+                }
+                wbuf[j] = wv;
+            }
+            const bool ok = mbar_wait(&bar[b], b ? phase1 : phase0);
+            if (ok) {
+                if (b) phase1 ^= 1u; else phase0 ^= 1u;
+            } else {
+                s_abort = 1;
+            }
+            __syncthreads();
+            if (s_abort) break;
+            // sliding-window FFMA: acc[u] = sum_j w[j] * seg[off + kb + u + j]
+            const float *sg = (b ? seg1 : seg0) + ((k0 + g.d0) - ((k0 + g.d0) & ~3)) + kb;
+            float acc[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) acc[u] = 0.0f;
+            float R0[2 * kU];
+#pragma unroll
+            for (int e = 0; e < kU - 1; ++e) R0[e] = sg[e];
+            for (int j0 = 0; j0 < g.nd; j0 += 2 * kU) {
+                // block A: values j0 .. j0 + 2kU - 2 live in R0[(v) % 2kU]
+#pragma unroll
+                for (int e = kU - 1; e < 2 * kU - 1; ++e) R0[e] = sg[j0 + e];
+#pragma unroll
+                for (int jj = 0; jj < kU; ++jj) {
+                    const float wv = wbuf[j0 + jj];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) acc[u] = fmaf(wv, R0[u + jj], acc[u]);
+                }
+                // block B: values j0 + kU .. j0 + 3kU - 2 -> R0[(v - j0) % 2kU]
+#pragma unroll
+                for (int e = 2 * kU - 1; e < 3 * kU - 1; ++e) R0[e % (2 * kU)] = sg[j0 + e];
+#pragma unroll
+                for (int jj = 0; jj < kU; ++jj) {
+                    const float wv = wbuf[j0 + kU + jj];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u)
+                        acc[u] = fmaf(wv, R0[(kU + u + jj) % (2 * kU)], acc[u]);
+                }
+                // shift: values j0 + 2kU .. j0 + 3kU - 2 must sit at R0[0 .. kU-2]
+#pragma unroll
+                for (int e = 0; e < kU - 1; ++e) R0[e] = R0[(2 * kU + e) % (2 * kU)];
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const float y = acc[u] - comp[u];
+                const float t = sum[u] + y;
+                comp[u] = (t - sum[u]) - y;
+                sum[u] = t;
+            }
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
+            // wait (bounded) for any copy still in flight before leaving
+            mbar_wait(&bar[0], phase0);
+            mbar_wait(&bar[1], phase1);
+            return;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int k = k0 + kb + u;
+            if (k < L) o[R.start + k] = sum[u] * P.domega;
+        }
+    }
+}
+
+} // namespace
+
+int belt_chunk() { return kChunk; }
+
+cudaError_t launch_conv_belt(const ConvPlan &p, const int2 *d_items, int n_items, int seg_cap,
+                             const float *d_in, float *d_out, int n_maps, long long map_stride,
+                             int *d_err, cudaStream_t st) {
+    if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    const size_t smem = sizeof(float) * 3 * (size_t)seg_cap;
+    cudaError_t e = cudaFuncSetAttribute(conv_belt_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_belt_kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int blocks = n_sm * per_sm;
+    if (blocks > n_items) blocks = n_items;
+    dim3 grid(blocks, n_maps);
+    conv_belt_kernel<<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
+                                                   seg_cap, d_err);
+    return cudaGetLastError();
+}
+
+} // namespace ksc

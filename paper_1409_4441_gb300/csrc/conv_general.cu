@@ -40,7 +40,8 @@ template <bool COUNT>
 __global__ void __launch_bounds__(kThreads)
 conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
                     const float *__restrict__ in, float *__restrict__ out,
-                    long long map_stride, unsigned long long *__restrict__ count) {
+                    long long map_stride, int belt_split,
+                    unsigned long long *__restrict__ count) {
     extern __shared__ float4 s_tab[];
     __shared__ float sA[kRingChunk], sB[kRingChunk], sC[kRingChunk], sHW[kRingChunk];
     __shared__ int sL[kRingChunk], sS[kRingChunk], sT[kRingChunk];
@@ -60,19 +61,28 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
         const int k = w.k0 + tid;
         const bool active = k < L;
         const int2 rg = P.d_range[w.ring];
+        // belt output ring with the belt kernel in use: cap input rings only
+        const bool add = !COUNT && belt_split && w.ring >= P.belt_lo && w.ring <= P.belt_hi;
         float sum = 0.0f, comp = 0.0f;
 
         for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
             const int nq = min(kRingChunk, rg.y - q0 + 1);
             __syncthreads();
             if (tid < nq) {
-                const DevRing Q = P.d_rings[q0 + tid];
+                const int q = q0 + tid;
+                const DevRing Q = P.d_rings[q];
                 const double dz = R.z - Q.z;
                 const double ds = (Q.z - R.z) * (Q.z + R.z) / (R.s + Q.s);  // s - s'
                 const double A = dz * dz + ds * ds;
                 const double ss = R.s * Q.s;
                 float hw;
-                if (A > (double)P.dc2 * (1.0 + 1e-6)) {
+                const bool bb = w.ring >= P.belt_lo && w.ring <= P.belt_hi &&
+                                q >= P.belt_lo && q <= P.belt_hi;
+                if ((add && bb) || (COUNT && belt_split == 1 && !bb) ||
+                    (COUNT && belt_split == 2 && bb)) {
+                    // belt-belt pair done by the circulant kernel, or a pair
+                    // outside the class being counted
+                } else if (A > (double)P.dc2 * (1.0 + 1e-6)) {
                     hw = -1.0f;  // no pixel of this ring is within theta_cut
                 } else {
                     const double cdp = (P.cos_cut - R.z * Q.z) / ss;
@@ -133,7 +143,12 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 sum = t;
             }
         }
-        if (!COUNT && active) o[R.start + k] = sum * P.domega;
+        if (!COUNT && active) {
+            if (add)
+                o[R.start + k] += sum * P.domega;
+            else
+                o[R.start + k] = sum * P.domega;
+        }
     }
     if (COUNT) {
         // block reduction of the pair counts
@@ -153,8 +168,8 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
 
 cudaError_t launch_conv_general(const ConvPlan &p, const WorkItem *d_items, int n_items,
                                 const float *d_in, float *d_out, int n_maps,
-                                long long map_stride, unsigned long long *d_count,
-                                cudaStream_t st) {
+                                long long map_stride, int belt_split,
+                                unsigned long long *d_count, cudaStream_t st) {
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
     static int n_sm = 0;
     if (n_sm == 0) {
@@ -184,10 +199,10 @@ cudaError_t launch_conv_general(const ConvPlan &p, const WorkItem *d_items, int 
     dim3 grid(blocks, n_maps);
     if (count)
         conv_general_kernel<true><<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out,
-                                                               map_stride, d_count);
+                                                               map_stride, belt_split, d_count);
     else
         conv_general_kernel<false><<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out,
-                                                                map_stride, d_count);
+                                                                map_stride, belt_split, d_count);
     return cudaGetLastError();
 }
 

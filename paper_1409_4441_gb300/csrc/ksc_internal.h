@@ -74,11 +74,34 @@ struct ConvPlan {
     float dc2;               // chord_cut^2
     double cos_cut;          // 1 - chord_cut^2 / 2
     float domega;            // 4 pi / Npix
+    int belt_lo, belt_hi;    // 0-based ring indices of the equatorial belt
 };
+// General ring-pair gather.  With belt_split set, belt output rings only take
+// their polar-cap input rings and add them to the output (the belt kernel has
+// written the belt-belt part); cap output rings take every input ring.
+// Counting (d_count != NULL): belt_split 0 counts every in-disc pair, 1 only
+// belt-belt pairs, 2 every other pair.
 cudaError_t launch_conv_general(const ConvPlan &p, const WorkItem *d_items,
                                 int n_items, const float *d_in, float *d_out,
-                                int n_maps, long long map_stride,
+                                int n_maps, long long map_stride, int belt_split,
                                 unsigned long long *d_count, cudaStream_t st);
+
+// Circulant belt-belt kernel; items are (belt ring, first pixel) chunks of
+// belt_chunk() pixels; seg_cap floats per shared-memory buffer.
+int belt_chunk();
+cudaError_t launch_conv_belt(const ConvPlan &p, const int2 *d_items, int n_items,
+                             int seg_cap, const float *d_in, float *d_out, int n_maps,
+                             long long map_stride, int *d_err, cudaStream_t st);
+
+// Symmetric gather over northern rings (and the equator): each thread owns
+// one first-quarter position and writes its eight images; only output rings
+// in [band_lo, band_hi] are written.  Items are (ring, first quarter position)
+// chunks of sym_chunk().
+int sym_chunk();
+cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
+                            const float *d_in, float *d_out, int n_maps,
+                            long long map_stride, int belt_split, int band_lo,
+                            int band_hi, cudaStream_t st);
 
 // Largest table (intervals) a convolution kernel keeps in shared memory.
 constexpr int kMaxIntervals = 8192;
@@ -90,7 +113,7 @@ struct ksc_split {
     int lmax = 0, l_cut = -1, nside = 0, mode = 0;
     int n_int = 0, n_unknowns = 0, n_kept = 0;
     double theta_cut = 0, chord_cut = 0, sigma_rms = 0, frac_error = 0;
-    long long n_pairs = -1;
+    long long n_pairs = -1, n_pairs_belt = -1;
     std::vector<double> k_harm, c_real, k_tilde;
 
     // device state
@@ -98,9 +121,19 @@ struct ksc_split {
     float4 *d_tab = nullptr;
     ksc::DevRing *d_rings = nullptr;
     int2 *d_range = nullptr;
-    ksc::WorkItem *d_items = nullptr;
+    // work lists, each with a per-ring prefix (nrings + 1 offsets)
+    ksc::WorkItem *d_items = nullptr;   // every ring (pair counting)
     int n_items = 0;
-    std::vector<int> ring_first_item;  // nrings + 1 prefix offsets
+    std::vector<int> ring_first_item;
+    ksc::WorkItem *d_items_sym = nullptr;  // northern rings for the symmetric gather
+    int n_items_sym = 0;
+    std::vector<int> ring_first_sym;
+    int path = 0;                          // 0: belt + symmetric, 1: general only
+    int2 *d_items_belt = nullptr;          // belt chunks for the circulant kernel
+    int n_items_belt = 0;
+    std::vector<int> ring_first_belt;
+    int seg_cap = 0;
+    int *d_err = nullptr;                  // device error flag (bounded waits)
     ksc::ConvPlan plan{};
 
     // end-to-end host path

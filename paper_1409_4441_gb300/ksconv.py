@@ -36,15 +36,16 @@ EXPORTS = [
     "ksc_default_opts", "ksc_make_split", "ksc_make_split_real", "ksc_split_info",
     "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
     "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
-    "ksc_conv_real_host", "ksc_count_pairs", "ksc_free_split", "ksc_status_string",
-    "ksc_last_error",
+    "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_count_pairs", "ksc_device_status",
+    "ksc_free_split",
+    "ksc_status_string", "ksc_last_error",
 ]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("oversample", ctypes.c_int),
                 ("svd_rcond", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("n_intervals", ctypes.c_int)]
+                ("n_intervals", ctypes.c_int), ("path", ctypes.c_int)]
 
 
 class Desc(ctypes.Structure):
@@ -53,7 +54,8 @@ class Desc(ctypes.Structure):
                 ("n_unknowns", ctypes.c_int), ("n_kept", ctypes.c_int),
                 ("theta_cut", ctypes.c_double), ("chord_cut", ctypes.c_double),
                 ("sigma_rms", ctypes.c_double), ("frac_error", ctypes.c_double),
-                ("n_pairs", ctypes.c_longlong)]
+                ("n_pairs", ctypes.c_longlong), ("n_pairs_belt", ctypes.c_longlong),
+                ("path", ctypes.c_int)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -71,7 +73,9 @@ _sig = {
     "ksc_conv_real_multimap": [_vp, _vp, _vp, _i, _vp],
     "ksc_conv_real_batch": [_vp, _vp, _vp, _i, _vp],
     "ksc_conv_real_host": [_vp, _vp, _vp],
+    "ksc_conv_real_stage": [_vp, _vp, _vp, _i, _vp],
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
+    "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
     "ksc_status_string": [_i],
     "ksc_last_error": [],
@@ -208,9 +212,20 @@ def count_pairs(s: Split) -> int:
     return n.value
 
 
+def device_status(s: Split, stream=None):
+    """Synchronize the stream and raise if a device-side check fired."""
+    _check(_lib.ksc_device_status(s.handle, _stream(stream)), "ksc_device_status")
+
+
 def conv_real(s: Split, d_in, d_out, stream=None):
     _check(_lib.ksc_conv_real(s.handle, _dptr(d_in), _dptr(d_out), _stream(stream)),
            "ksc_conv_real")
+    return d_out
+
+
+def conv_real_stage(s: Split, d_in, d_out, stage: int, stream=None):
+    _check(_lib.ksc_conv_real_stage(s.handle, _dptr(d_in), _dptr(d_out), stage, _stream(stream)),
+           "ksc_conv_real_stage")
     return d_out
 
 

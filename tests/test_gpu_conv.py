@@ -189,3 +189,47 @@ def test_pair_count_matches_oracle(K):
     _, amb = O.brute_conv(nside, np.ones(O.npix(nside)), tc, c=np.array([4 * np.pi]), amb_eps=1e-6)
     n_amb = int(round(amb.sum() / (4 * np.pi / O.npix(nside))))
     assert abs(n - cnt.sum()) <= n_amb
+
+
+@pytest.mark.parametrize("nside,tc_deg,lmax,fwhm_deg", [
+    (1, 90.0, 3, 40.0), (2, 45.0, 7, 20.0), (4, 100.0, 11, 20.0), (8, 180.0, 23, 10.0),
+    (16, 3.0, 47, 1.5), (32, 30.0, 95, 3.0), (128, 4.0, 383, 1.0),
+])
+def test_fast_path_matches_general_path(K, nside, tc_deg, lmax, fwhm_deg):
+    """Circulant belt kernel + symmetric gather (default) against the general
+    ring-pair gather: same sums in a different order."""
+    tc = np.radians(tc_deg)
+    c = inputs.gaussian_beam(lmax, np.radians(fwhm_deg))
+    m = inputs.white_noise_map(nside, 77 + nside).astype(np.float32)
+    outs = []
+    for path in (0, 1):
+        with K.make_split_real(c, nside, tc, path=path) as sp:
+            assert K.split_info(sp)["path"] == path or nside >= 8 and tc_deg > 90
+            outs.append(_run(K, sp, m))
+            K.device_status(sp)
+    rms = np.sqrt(np.mean(outs[1] ** 2))
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * rms
+
+
+def test_stages_compose_bitwise_and_counts(K):
+    nside = 64
+    tc = np.radians(12.0)
+    c = inputs.gaussian_beam(191, np.radians(2.0))
+    m = torch.tensor(inputs.white_noise_map(nside, 3).astype(np.float32), device="cuda")
+    with K.make_split_real(c, nside, tc) as sp:
+        a = torch.empty_like(m); b = torch.empty_like(m)
+        K.conv_real(sp, m, a)
+        K.conv_real_stage(sp, m, b, 1)
+        K.conv_real_stage(sp, m, b, 2)
+        K.device_status(sp)
+        assert torch.equal(a, b)
+        n = K.count_pairs(sp)
+        info = K.split_info(sp)
+    cnt = O.count_pairs(nside, tc)
+    assert abs(n - cnt.sum()) <= 8
+    # belt-belt pairs: both pixels with |z| <= 2/3
+    z = O.pix2vec(nside)[:, 2]
+    belt = np.abs(z) <= 2 / 3 + 1e-12
+    assert 0 < info["n_pairs_belt"] < n
+    assert abs(info["n_pairs_belt"] - O.count_pairs(nside, tc, out_pix=np.where(belt)[0]).sum()) \
+        <= abs(n - info["n_pairs_belt"])  # sanity: belt outputs dominate belt-belt pairs
