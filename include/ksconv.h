@@ -63,8 +63,10 @@ typedef struct {
     int oversample;    /* real-space unknowns: nodes of an oversample*(lmax+1)
                           point Gauss-Legendre rule inside the cap (z_cut of
                           Eq. 4); default 2                                    */
-    double svd_rcond;  /* singular values below svd_rcond * max are dropped
-                          (Sec. 2: 1e-6); default 1e-6                          */
+    double svd_rcond;  /* singular values of the normal matrix A^T W A of
+                          Eq. 3 below svd_rcond * max are dropped (those of
+                          W^{1/2} A below sqrt(svd_rcond) * max); Sec. 2
+                          uses 1e-6; default 1e-6                                */
     double alpha;      /* Eq. 6 numerical-error factor; default 5 (Sec. 3)     */
     int n_intervals;   /* K_r table intervals in the chord d in [0, d_cut];
                           0 = automatic (about 96 per shortest l_max

@@ -177,8 +177,10 @@ def split_lsq(K, lcut: int, theta_cut: float, cl_in=None, oversample: int = 2,
 
     x = [Khat_l (l <= l_cut); Khat_theta (z_cut values)] (Eq. 4); A = [delta | P]
     (Eq. 5) with lmax+1 rows (l = 0..lmax); W = diag((2l+1) C_l^in) (Eq. 5 with
-    the input spectrum of Eq. 2).  The SVD runs on W^{1/2} A with unit-norm
-    columns and drops singular values below rcond times the largest.
+    the input spectrum of Eq. 2).  As in Sec. 2, the SVD is taken of the normal
+    matrix A^T W A of Eq. 3 (columns of W^{1/2} A scaled to unit norm, so the
+    cut is scale-free) and singular values below rcond (1e-6) times the largest
+    are dropped.
 
     Returns a dict with k_harm (l <= l_cut), x (real-space unknowns), the
     Legendre coefficients c_real (l <= lmax) of the real-space part before
@@ -198,9 +200,12 @@ def split_lsq(K, lcut: int, theta_cut: float, cl_in=None, oversample: int = 2,
     b = sw * K
     cn = np.linalg.norm(B, axis=0)
     cn[cn == 0] = 1.0
-    U, s, Vt = np.linalg.svd(B / cn, full_matrices=False)
+    Bn = B / cn
+    N = Bn.T @ Bn                      # A^T W A, unit diagonal
+    rhs = Bn.T @ b                     # A^T W K
+    U, s, Vt = np.linalg.svd(N)
     keep = s > rcond * s[0]
-    y = (Vt[keep].T @ ((U[:, keep].T @ b) / s[keep])) / cn
+    y = (Vt[keep].T @ ((U[:, keep].T @ rhs) / s[keep])) / cn
     k_harm = y[:nh]
     x = y[nh:]
     c_real = 2.0 * np.pi * (Pj.T @ (wj * x))

@@ -106,7 +106,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         const bool belt = r >= belt_lo && r <= belt_hi;
         const bool reaches_cap = range[r].x < belt_lo || range[r].y > belt_hi;
         if (r <= eq && (!belt || reaches_cap || o.path == 1))
-            for (int k0 = 0; k0 < g.len[r] / 4; k0 += ksc::sym_chunk()) items_sym.push_back({r, k0});
+            for (int k0 = 0; k0 < ksc::sym_classes(g.len[r], g.phase[r]); k0 += ksc::sym_chunk())
+                items_sym.push_back({r, k0});
         if (belt) {
             for (int k0 = 0; k0 < g.len[r]; k0 += bc) items_belt.push_back(make_int2(r, k0));
             // widest circulant window of this ring (same arithmetic as the kernel)
@@ -188,8 +189,13 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     p.n_int = n_int;
     p.inv_h = (float)(n_int / s->chord_cut);
     p.dc2 = (float)(s->chord_cut * s->chord_cut);
-    // theta_cut = pi: every pair, whatever the FP32 rounding of antipodal chords
-    if (s->theta_cut >= kPi) p.dc2 = 5.0f;
+    p.scale2 = ((double)n_int / s->chord_cut) * ((double)n_int / s->chord_cut);
+    p.nint2 = (float)((double)n_int * (double)n_int);
+    // theta_cut = pi: every pair, whatever the rounding of antipodal chords
+    if (s->theta_cut >= kPi) {
+        p.dc2 = 5.0f;
+        p.nint2 = (float)(1.25 * (double)n_int * (double)n_int);
+    }
     p.cos_cut = 1.0 - 0.5 * s->chord_cut * s->chord_cut;
     p.domega = (float)(4.0 * kPi / (double)p.npix);
     p.belt_lo = belt_lo;

@@ -24,6 +24,7 @@
 // flag and the kernel stops work instead of hanging.
 #include <cstdint>
 
+#include "ksc_device.cuh"
 #include "ksc_internal.h"
 
 namespace ksc {
@@ -34,18 +35,6 @@ constexpr int kThreads = 160;   // 5 warps
 constexpr int kChunk = kU * kThreads;
 constexpr int kMaxWait = 1 << 22;   // mbarrier polls before giving up
 constexpr double kPi = 3.14159265358979323846;
-
-__device__ __forceinline__ float sin_taylor(float x) {
-    const float x2 = x * x;
-    float p = 1.6059043836821613e-10f;
-    p = fmaf(p, x2, -2.5052108385441720e-08f);
-    p = fmaf(p, x2, 2.7557319223985893e-06f);
-    p = fmaf(p, x2, -1.9841269841269841e-04f);
-    p = fmaf(p, x2, 8.3333333333333333e-03f);
-    p = fmaf(p, x2, -1.6666666666666667e-01f);
-    p = fmaf(p, x2, 1.0f);
-    return x * p;
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -86,7 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 }
 
 struct PairGeom {
-    float A, B, cs;     // chord^2 = A + B sin^2(x), x = (t - t' - 2 Delta) * cs
+    DF A, B, c1;        // (chord n_int/d_cut)^2 = A + B sin^2(x), x = (t - t' - 2 Delta) c1
     int d0;             // first Delta of the padded window
     int nd;             // padded window length (multiple of 2 kU)
     int exact_lo, exact_hi;  // Delta range that may carry weight (at most L values)
@@ -94,16 +83,17 @@ struct PairGeom {
     bool empty;
 };
 
-__device__ PairGeom pair_geom(const DevRing &R, const DevRing &Q, double cos_cut, float dc2) {
+__device__ PairGeom pair_geom(const DevRing &R, const DevRing &Q, double cos_cut, float dc2,
+                              double scale2) {
     PairGeom g;
     const int L = R.len;
     const double dz = R.z - Q.z;
     const double ds = (Q.z - R.z) * (Q.z + R.z) / (R.s + Q.s);
     const double A = dz * dz + ds * ds;
     const double ss = R.s * Q.s;
-    g.A = (float)A;
-    g.B = (float)(4.0 * ss);
-    g.cs = (float)(kPi / (2.0 * L));
+    g.A = df_from_double(A * scale2);
+    g.B = df_from_double(4.0 * ss * scale2);
+    g.c1 = df_from_double(kPi / (2.0 * L));
     g.tdiff = R.phase - Q.phase;
     g.empty = A > (double)dc2 * (1.0 + 1e-6);
     double cdp = (cos_cut - R.z * Q.z) / ss;
@@ -162,7 +152,7 @@ conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
         // issue the copy of input ring q into buffer b
         auto issue = [&](int q, int b) {
             const DevRing Q = P.d_rings[q];
-            PairGeom g = pair_geom(R, Q, P.cos_cut, P.dc2);
+            PairGeom g = pair_geom(R, Q, P.cos_cut, P.dc2, P.scale2);
             s_g[b] = g;
             if (g.empty) return;
             // ring coordinates [a, a + n), a aligned down to 4 floats
@@ -202,15 +192,13 @@ conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
                 const int D = g.d0 + j;
                 float wv = 0.0f;
                 if (D >= g.exact_lo && D <= g.exact_hi) {
-                    const float sn = sin_taylor((float)(g.tdiff - 2 * D) * g.cs);
-                    const float d2 = fmaf(g.B, sn * sn, g.A);
-                    if (d2 <= P.dc2) {
-                        const float uu = sqrtf(d2) * P.inv_h;
-                        const int i = min((int)uu, P.n_int - 1);
-                        const float f = uu - (float)i;
-                        const float4 c = __ldg(&P.d_tab[i]);
-                        wv = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
-                    }
+                    const float mf = (float)(g.tdiff - 2 * D);
+                    const float xh = mf * g.c1.h;
+                    const float xl = fmaf(mf, g.c1.h, -xh) + mf * g.c1.l;
+                    int ti;
+                    float f;
+                    if (chord_to_table(g.A, g.B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f))
+                        wv = hermite(__ldg(&P.d_tab[ti]), f);
                 }
                 wbuf[j] = wv;
             }

@@ -15,6 +15,7 @@
 // FP32 rounding on |x| <= pi/2.  K_r(d) comes from the cubic Hermite table in
 // shared memory; each input ring's FP32 partial sum is folded into the pixel
 // total with Kahan compensation.
+#include "ksc_device.cuh"
 #include "ksc_internal.h"
 
 namespace ksc {
@@ -24,18 +25,6 @@ constexpr int kThreads = 256;
 constexpr int kRingChunk = 128;
 constexpr double kPi = 3.14159265358979323846;
 
-__device__ __forceinline__ float sin_taylor(float x) {
-    const float x2 = x * x;
-    float p = 1.6059043836821613e-10f;       //  1/13!
-    p = fmaf(p, x2, -2.5052108385441720e-08f); // -1/11!
-    p = fmaf(p, x2, 2.7557319223985893e-06f);  //  1/9!
-    p = fmaf(p, x2, -1.9841269841269841e-04f); // -1/7!
-    p = fmaf(p, x2, 8.3333333333333333e-03f);  //  1/5!
-    p = fmaf(p, x2, -1.6666666666666667e-01f); // -1/3!
-    p = fmaf(p, x2, 1.0f);
-    return x * p;
-}
-
 template <bool COUNT>
 __global__ void __launch_bounds__(kThreads)
 conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
@@ -43,7 +32,8 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     long long map_stride, int belt_split,
                     unsigned long long *__restrict__ count) {
     extern __shared__ float4 s_tab[];
-    __shared__ float sA[kRingChunk], sB[kRingChunk], sC[kRingChunk], sHW[kRingChunk];
+    __shared__ DF sA[kRingChunk], sB[kRingChunk], sC[kRingChunk];
+    __shared__ float sHW[kRingChunk];
     __shared__ int sL[kRingChunk], sS[kRingChunk], sT[kRingChunk];
 
     const int tid = threadIdx.x;
@@ -82,6 +72,7 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     (COUNT && belt_split == 2 && bb)) {
                     // belt-belt pair done by the circulant kernel, or a pair
                     // outside the class being counted
+                    hw = -1.0f;
                 } else if (A > (double)P.dc2 * (1.0 + 1e-6)) {
                     hw = -1.0f;  // no pixel of this ring is within theta_cut
                 } else {
@@ -89,9 +80,9 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : acos(cdp));
                     hw = (float)(dphi * Q.len / (2.0 * kPi)) + 1.0f;
                 }
-                sA[tid] = (float)A;
-                sB[tid] = (float)(4.0 * ss);
-                sC[tid] = (float)(kPi / (2.0 * (double)L * (double)Q.len));
+                sA[tid] = df_from_double(A * P.scale2);
+                sB[tid] = df_from_double(4.0 * ss * P.scale2);
+                sC[tid] = df_from_double(kPi / (2.0 * (double)L * (double)Q.len));
                 sHW[tid] = hw;
                 sL[tid] = Q.len;
                 sS[tid] = Q.start;
@@ -115,22 +106,20 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 int N = (int)(num - 2LL * klo * L);
                 int idx = klo % L2;
                 if (idx < 0) idx += L2;
-                const float A = sA[qi], B = sB[qi], cs = sC[qi];
+                const DF A = sA[qi], B = sB[qi], cs = sC[qi];
                 const float *mr = m + sS[qi];
                 float part = 0.0f;
                 for (int kk = klo; kk <= khi; ++kk) {
-                    const float sn = sin_taylor((float)N * cs);
-                    const float d2 = fmaf(B, sn * sn, A);
-                    if (d2 <= P.dc2) {
+                    const float Nf = (float)N;
+                    const float xh = Nf * cs.h;
+                    const float xl = fmaf(Nf, cs.h, -xh) + Nf * cs.l;
+                    int ti;
+                    float f;
+                    if (chord_to_table(A, B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f)) {
                         if (COUNT) {
                             ++cnt;
                         } else {
-                            const float u = sqrtf(d2) * P.inv_h;
-                            const int i = min((int)u, P.n_int - 1);
-                            const float f = u - (float)i;
-                            const float4 c = s_tab[i];
-                            const float kv = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
-                            part = fmaf(kv, __ldg(mr + idx), part);
+                            part = fmaf(hermite(s_tab[ti], f), __ldg(mr + idx), part);
                         }
                     }
                     N -= 2 * L;

@@ -1,0 +1,84 @@
+// Device arithmetic shared by the convolution kernels.
+//
+// Chord -> table position, carried in "double-float" (an FP32 pair hi + lo,
+// about 44 significant bits) so that the kernel argument is as accurate as the
+// FP32 table itself.  For a pair of pixels on rings (z, s) and (z', s') that are
+// dphi apart, chord^2 = A + B sin^2(dphi/2), A = (z - z')^2 + (s - s')^2,
+// B = 4 s s'.  Scaling both by (n_int / d_cut)^2 gives the table position
+// directly: u = d n_int / d_cut = sqrt(A' + B' sin^2 x), interval floor(u),
+// offset u - floor(u), and the cut d <= d_cut is u^2 <= n_int^2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ksc {
+
+struct DF {  // hi + lo
+    float h, l;
+};
+
+// Split an FP64 value into an FP32 pair.
+__host__ __device__ inline DF df_from_double(double v) {
+    DF r;
+    r.h = (float)v;
+    r.l = (float)(v - (double)r.h);
+    return r;
+}
+
+// sin(x) for x = xh + xl, |x| <= pi/2 + small, as a pair (xh, lo): the leading
+// term x is carried exactly and only the Taylor tail x^3 (-1/3! + x^2/5! - ...)
+// (to x^13) and the xl cos(x) correction are rounded.
+__device__ __forceinline__ DF sin_df(float xh, float xl) {
+    const float x2 = xh * xh;
+    float q = 1.6059043836821613e-10f;         //  1/13!
+    q = fmaf(q, x2, -2.5052108385441720e-08f); // -1/11!
+    q = fmaf(q, x2, 2.7557319223985893e-06f);  //  1/9!
+    q = fmaf(q, x2, -1.9841269841269841e-04f); // -1/7!
+    q = fmaf(q, x2, 8.3333333333333333e-03f);  //  1/5!
+    q = fmaf(q, x2, -1.6666666666666667e-01f); // -1/3!
+    const float c = fmaf(x2, fmaf(x2, 4.1666666666666664e-02f, -0.5f), 1.0f);  // ~cos
+    DF s;
+    s.h = xh;
+    s.l = fmaf(xh * x2, q, xl * c);
+    return s;
+}
+
+// Table position for chord^2 * (n_int/d_cut)^2 = A + B sin^2(x).
+// Returns false when the pair lies beyond the cut; otherwise interval i in
+// [0, n_int - 1] and offset f (about [0, 1]).
+__device__ __forceinline__ bool chord_to_table(DF A, DF B, DF s, float nint2, int n_int,
+                                               int *i_out, float *f_out) {
+    // s^2
+    const float s2h = s.h * s.h;
+    const float s2l = fmaf(2.0f * s.h, s.l, fmaf(s.h, s.h, -s2h));
+    // B s^2
+    const float ph = B.h * s2h;
+    const float pl = fmaf(B.h, s2h, -ph) + fmaf(B.h, s2l, B.l * s2h);
+    // D = A + B s^2 (two-sum on the high parts)
+    const float dh = A.h + ph;
+    const float bp = dh - A.h;
+    const float e = (A.h - (dh - bp)) + (ph - bp);
+    const float dl = e + A.l + pl;
+    if (dh > nint2) return false;
+    // u = sqrt(D): approximate reciprocal square root, then one double-float
+    // Newton correction u = uh + (D - uh^2) / (2 uh)
+    const float r = rsqrtf(fmaxf(dh, 1e-30f));
+    const float uh = dh * r;
+    const float ul = (fmaf(-uh, uh, dh) + dl) * (0.5f * r);
+    // floor(uh) by the 1.5 * 2^23 rounding trick (uh < 2^22)
+    const float t = (uh - 0.5f) + 12582912.0f;
+    float fi = t - 12582912.0f;
+    int i = __float_as_int(t) - 0x4B400000;
+    const float top = (float)(n_int - 1);
+    if (fi > top) { fi = top; i = n_int - 1; }
+    if (fi < 0.0f) { fi = 0.0f; i = 0; }
+    *i_out = i;
+    *f_out = (uh - fi) + ul;
+    return true;
+}
+
+__device__ __forceinline__ float hermite(const float4 c, float f) {
+    return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+}
+
+} // namespace ksc

@@ -75,6 +75,8 @@ struct ConvPlan {
     double cos_cut;          // 1 - chord_cut^2 / 2
     float domega;            // 4 pi / Npix
     int belt_lo, belt_hi;    // 0-based ring indices of the equatorial belt
+    double scale2;           // (n_int / chord_cut)^2: chord^2 -> table position^2
+    float nint2;             // the cut in table-position^2 units (n_int^2)
 };
 // General ring-pair gather.  With belt_split set, belt output rings only take
 // their polar-cap input rings and add them to the output (the belt kernel has
@@ -98,6 +100,7 @@ cudaError_t launch_conv_belt(const ConvPlan &p, const int2 *d_items, int n_items
 // in [band_lo, band_hi] are written.  Items are (ring, first quarter position)
 // chunks of sym_chunk().
 int sym_chunk();
+int sym_classes(int len, int phase);  // reflection classes of a ring's first quarter
 cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
                             const float *d_in, float *d_out, int n_maps,
                             long long map_stride, int belt_split, int band_lo,

@@ -11,8 +11,9 @@
 // Solve (Eq. 3): every row l <= l_cut has its own free unknown Khat_l, so those
 // rows are fitted exactly (Khat_l = K_l - (A x)_l) and the minimisation of
 // Eq. 2 reduces to the rows l > l_cut.  That block, W^{1/2} A with unit-norm
-// columns, is solved by SVD (Householder QR, then one-sided Jacobi on R), with
-// singular values below rcond * max dropped (Sec. 2: 1e-6).
+// columns, is solved by SVD (Householder QR, then one-sided Jacobi on R).  The
+// cut of Sec. 2 (1e-6) is on the singular values of the normal matrix of
+// Eq. 3, i.e. W^{1/2} A's singular values below sqrt(rcond) * max are dropped.
 //
 // The resulting real-space kernel is K_r(z) = sum_l (2l+1)/(4 pi) c_l P_l(z)
 // for z >= cos(theta_cut), c_l = 2 pi sum_j w_j x_j P_l(z_j), zero outside.
@@ -283,10 +284,13 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
         sig[j] = std::sqrt(s);
         smax = std::max(smax, sig[j]);
     }
+    // The cut of Sec. 2 applies to the singular values of the normal matrix
+    // A^T W A (Eq. 3), the squares of those of W^{1/2} A.
+    const double cut = std::sqrt(rcond) * smax;
     std::vector<double> y(nz, 0.0);
     int kept = 0;
     for (int j = 0; j < nz; ++j) {
-        if (!(sig[j] > rcond * smax)) continue;
+        if (!(sig[j] > cut)) continue;
         ++kept;
         double d = 0;
         for (int k = 0; k < p; ++k) d += R[(size_t)j * p + k] * cvec[k];
