@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "ksc_device.cuh"
 #include "ksc_internal.h"
 
 namespace {
@@ -41,6 +42,8 @@ void release(ksc_split *s) {
     cudaFree(s->d_tab);
     cudaFree(s->d_rings);
     cudaFree(s->d_range);
+    cudaFree(s->d_pairs);
+    cudaFree(s->d_pair_base);
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
     cudaFree(s->d_items_belt);
@@ -56,7 +59,10 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     s->chord_cut = 2.0 * std::sin(0.5 * s->theta_cut);
     int n_int = o.n_intervals;
     if (n_int <= 0) {
-        double want = 96.0 * s->chord_cut * std::max(s->lmax, 1) / (2.0 * kPi);
+        // ~96 intervals per shortest l_max wavelength; the chord compresses
+        // theta by cos(theta/2), so wide cuts need proportionally more
+        const double squeeze = std::max(std::cos(0.5 * s->theta_cut), 1e-3);
+        double want = 96.0 * s->chord_cut * std::max(s->lmax, 1) / (2.0 * kPi * squeeze);
         n_int = (int)std::ceil(want);
         n_int = std::max(256, std::min(n_int, ksc::kMaxIntervals));
     }
@@ -116,7 +122,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                 double ss = g.s[r] * g.s[q];
                 double cdp = (1.0 - 0.5 * s->chord_cut * s->chord_cut - g.z[r] * g.z[q]) / ss;
                 double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : std::acos(cdp));
-                int w = (int)std::ceil(dphi * L / (2.0 * kPi)) + 1;
+                int w = (int)std::ceil(dphi * L / (2.0 * kPi)) + 1;  // same as PairInfo::w
                 int n = std::min(2 * w + 1, L);
                 max_nd = std::max(max_nd, n);
             }
@@ -143,8 +149,48 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         s->seg_cap = 0;
     }
 
+    // Ring-pair geometry (FP64 on the host, once per split).
+    std::vector<int> pair_base(nr + 1, 0);
+    for (int r = 0; r < nr; ++r) pair_base[r + 1] = pair_base[r] + (range[r].y - range[r].x + 1);
+    std::vector<ksc::PairInfo> pairs((size_t)pair_base[nr]);
+    {
+        const double dc = s->chord_cut;
+        const double cos_cut = 1.0 - 0.5 * dc * dc;
+        const double scale2 = ((double)n_int / dc) * ((double)n_int / dc);
+        const double dc2 = s->theta_cut >= kPi ? 5.0 : dc * dc;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int r = 0; r < nr; ++r) {
+            for (int q = range[r].x; q <= range[r].y; ++q) {
+                const double dz = g.z[r] - g.z[q];
+                const double ds = (g.z[q] - g.z[r]) * (g.z[q] + g.z[r]) / (g.s[r] + g.s[q]);
+                const double A = dz * dz + ds * ds;
+                const double ss = g.s[r] * g.s[q];
+                const int Lq = g.len[q];
+                ksc::PairInfo pi;
+                const ksc::DF a = ksc::df_from_double(A * scale2);
+                const ksc::DF b = ksc::df_from_double(4.0 * ss * scale2);
+                const ksc::DF c = ksc::df_from_double(kPi / (2.0 * (double)g.len[r] * (double)Lq));
+                pi.Ah = a.h; pi.Al = a.l; pi.Bh = b.h; pi.Bl = b.l; pi.ch = c.h; pi.cl = c.l;
+                if (A > dc2 * (1.0 + 1e-6)) {
+                    pi.hw = -1.0f;
+                    pi.w = -1;
+                } else {
+                    const double cdp = (cos_cut - g.z[r] * g.z[q]) / ss;
+                    const double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : std::acos(cdp));
+                    pi.hw = (float)(dphi * Lq / (2.0 * kPi)) + 1.0f;
+                    pi.w = (int)std::ceil(dphi * Lq / (2.0 * kPi)) + 1;
+                }
+                pairs[(size_t)pair_base[r] + (q - range[r].x)] = pi;
+            }
+        }
+    }
+
     cudaError_t e;
     cudaGetDevice(&s->device);
+    if ((e = dev_upload(&s->d_pairs, pairs.data(), pairs.size())) != cudaSuccess)
+        return cuda_fail(e, "upload ring-pair table");
+    if ((e = dev_upload(&s->d_pair_base, pair_base.data(), pair_base.size())) != cudaSuccess)
+        return cuda_fail(e, "upload ring-pair offsets");
     if ((e = dev_upload(&s->d_rings, rings.data(), rings.size())) != cudaSuccess)
         return cuda_fail(e, "upload ring table");
     if ((e = dev_upload(&s->d_range, range.data(), range.size())) != cudaSuccess)
@@ -185,6 +231,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     p.nrings = nr;
     p.d_rings = s->d_rings;
     p.d_range = s->d_range;
+    p.d_pairs = s->d_pairs;
+    p.d_pair_base = s->d_pair_base;
     p.d_tab = s->d_tab;
     p.n_int = n_int;
     p.inv_h = (float)(n_int / s->chord_cut);
@@ -200,6 +248,11 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     p.domega = (float)(4.0 * kPi / (double)p.npix);
     p.belt_lo = belt_lo;
     p.belt_hi = belt_hi;
+    {
+        const ksc::DF c1 = ksc::df_from_double(kPi / (2.0 * 4.0 * nside));
+        p.belt_c1h = c1.h;
+        p.belt_c1l = c1.l;
+    }
     return KSC_OK;
 }
 
@@ -266,6 +319,10 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
 }
 
 } // namespace
+
+namespace ksc {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+} // namespace ksc
 
 extern "C" {
 

@@ -34,7 +34,6 @@ constexpr int kU = 13;          // outputs per thread (odd: conflict-free stride
 constexpr int kThreads = 160;   // 5 warps
 constexpr int kChunk = kU * kThreads;
 constexpr int kMaxWait = 1 << 22;   // mbarrier polls before giving up
-constexpr double kPi = 3.14159265358979323846;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -83,24 +82,16 @@ struct PairGeom {
     bool empty;
 };
 
-__device__ PairGeom pair_geom(const DevRing &R, const DevRing &Q, double cos_cut, float dc2,
-                              double scale2) {
+// Window of a belt ring pair from its precomputed geometry.
+__device__ __forceinline__ PairGeom pair_geom(const PairInfo &pi, int L, int tdiff, float c1h,
+                                              float c1l) {
     PairGeom g;
-    const int L = R.len;
-    const double dz = R.z - Q.z;
-    const double ds = (Q.z - R.z) * (Q.z + R.z) / (R.s + Q.s);
-    const double A = dz * dz + ds * ds;
-    const double ss = R.s * Q.s;
-    g.A = df_from_double(A * scale2);
-    g.B = df_from_double(4.0 * ss * scale2);
-    g.c1 = df_from_double(kPi / (2.0 * L));
-    g.tdiff = R.phase - Q.phase;
-    g.empty = A > (double)dc2 * (1.0 + 1e-6);
-    double cdp = (cos_cut - R.z * Q.z) / ss;
-    double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : acos(cdp));
-    // |dphi| = |t - t' - 2 Delta| pi / L <= dphi_max  (plus one pixel of margin)
-    int w = (int)ceil(dphi * L / (2.0 * kPi)) + 1;
-    int lo = -w, hi = w;
+    g.A = DF{pi.Ah, pi.Al};
+    g.B = DF{pi.Bh, pi.Bl};
+    g.c1 = DF{c1h, c1l};
+    g.tdiff = tdiff;
+    g.empty = pi.w < 0;
+    int lo = -pi.w, hi = pi.w;
     if (hi - lo + 1 >= L) {  // whole ring: each input pixel exactly once
         lo = -(L / 2);
         hi = lo + L - 1;
@@ -150,9 +141,10 @@ conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
         for (int u = 0; u < kU; ++u) sum[u] = comp[u] = 0.0f;
 
         // issue the copy of input ring q into buffer b
+        const PairInfo *pinfo = P.d_pairs + P.d_pair_base[r] - rg.x;
         auto issue = [&](int q, int b) {
             const DevRing Q = P.d_rings[q];
-            PairGeom g = pair_geom(R, Q, P.cos_cut, P.dc2, P.scale2);
+            PairGeom g = pair_geom(pinfo[q], L, R.phase - Q.phase, P.belt_c1h, P.belt_c1l);
             s_g[b] = g;
             if (g.empty) return;
             // ring coordinates [a, a + n), a aligned down to 4 floats
@@ -212,9 +204,9 @@ conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
             if (s_abort) break;
             // sliding-window FFMA: acc[u] = sum_j w[j] * seg[off + kb + u + j]
             const float *sg = (b ? seg1 : seg0) + ((k0 + g.d0) - ((k0 + g.d0) & ~3)) + kb;
-            float acc[kU];
+            float acc[kU], ring[kU];  // block (2 kU steps) and ring-pair partial sums
 #pragma unroll
-            for (int u = 0; u < kU; ++u) acc[u] = 0.0f;
+            for (int u = 0; u < kU; ++u) acc[u] = ring[u] = 0.0f;
             float R0[2 * kU];
 #pragma unroll
             for (int e = 0; e < kU - 1; ++e) R0[e] = sg[e];
@@ -238,13 +230,16 @@ conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
                     for (int u = 0; u < kU; ++u)
                         acc[u] = fmaf(wv, R0[(kU + u + jj) % (2 * kU)], acc[u]);
                 }
-                // shift: values j0 + 2kU .. j0 + 3kU - 2 must sit at R0[0 .. kU-2]
+                // values j0 + 2kU .. j0 + 3kU - 2 already sit at R0[0 .. kU-2]
 #pragma unroll
-                for (int e = 0; e < kU - 1; ++e) R0[e] = R0[(2 * kU + e) % (2 * kU)];
+                for (int u = 0; u < kU; ++u) {
+                    ring[u] += acc[u];
+                    acc[u] = 0.0f;
+                }
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const float y = acc[u] - comp[u];
+                const float y = ring[u] - comp[u];
                 const float t = sum[u] + y;
                 comp[u] = (t - sum[u]) - y;
                 sum[u] = t;

@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kRingChunk = 128;
-constexpr double kPi = 3.14159265358979323846;
+
 
 template <bool COUNT>
 __global__ void __launch_bounds__(kThreads)
@@ -61,10 +61,7 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
             if (tid < nq) {
                 const int q = q0 + tid;
                 const DevRing Q = P.d_rings[q];
-                const double dz = R.z - Q.z;
-                const double ds = (Q.z - R.z) * (Q.z + R.z) / (R.s + Q.s);  // s - s'
-                const double A = dz * dz + ds * ds;
-                const double ss = R.s * Q.s;
+                const PairInfo pi = P.d_pairs[P.d_pair_base[w.ring] + (q - rg.x)];
                 float hw;
                 const bool bb = w.ring >= P.belt_lo && w.ring <= P.belt_hi &&
                                 q >= P.belt_lo && q <= P.belt_hi;
@@ -73,16 +70,12 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     // belt-belt pair done by the circulant kernel, or a pair
                     // outside the class being counted
                     hw = -1.0f;
-                } else if (A > (double)P.dc2 * (1.0 + 1e-6)) {
-                    hw = -1.0f;  // no pixel of this ring is within theta_cut
                 } else {
-                    const double cdp = (P.cos_cut - R.z * Q.z) / ss;
-                    double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : acos(cdp));
-                    hw = (float)(dphi * Q.len / (2.0 * kPi)) + 1.0f;
+                    hw = pi.hw;
                 }
-                sA[tid] = df_from_double(A * P.scale2);
-                sB[tid] = df_from_double(4.0 * ss * P.scale2);
-                sC[tid] = df_from_double(kPi / (2.0 * (double)L * (double)Q.len));
+                sA[tid] = DF{pi.Ah, pi.Al};
+                sB[tid] = DF{pi.Bh, pi.Bl};
+                sC[tid] = DF{pi.ch, pi.cl};
                 sHW[tid] = hw;
                 sL[tid] = Q.len;
                 sS[tid] = Q.start;
@@ -108,28 +101,31 @@ conv_general_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 if (idx < 0) idx += L2;
                 const DF A = sA[qi], B = sB[qi], cs = sC[qi];
                 const float *mr = m + sS[qi];
-                float part = 0.0f;
-                for (int kk = klo; kk <= khi; ++kk) {
-                    const float Nf = (float)N;
-                    const float xh = Nf * cs.h;
-                    const float xl = fmaf(Nf, cs.h, -xh) + Nf * cs.l;
-                    int ti;
-                    float f;
-                    if (chord_to_table(A, B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f)) {
-                        if (COUNT) {
-                            ++cnt;
-                        } else {
-                            part = fmaf(hermite(s_tab[ti], f), __ldg(mr + idx), part);
+                // blocks of 32 window steps, each Kahan-folded into the total
+                for (int kb0 = klo; kb0 <= khi; kb0 += 32) {
+                    const int kend = min(kb0 + 31, khi);
+                    float part = 0.0f;
+                    for (int kk = kb0; kk <= kend; ++kk) {
+                        const float Nf = (float)N;
+                        const float xh = Nf * cs.h;
+                        const float xl = fmaf(Nf, cs.h, -xh) + Nf * cs.l;
+                        int ti;
+                        float f;
+                        if (chord_to_table(A, B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f)) {
+                            if (COUNT) {
+                                ++cnt;
+                            } else {
+                                part = fmaf(hermite(s_tab[ti], f), __ldg(mr + idx), part);
+                            }
                         }
+                        N -= 2 * L;
+                        if (++idx == L2) idx = 0;
                     }
-                    N -= 2 * L;
-                    if (++idx == L2) idx = 0;
+                    const float y = part - comp;
+                    const float t = sum + y;
+                    comp = (t - sum) - y;
+                    sum = t;
                 }
-                // Kahan: fold this ring's partial sum into the total
-                const float y = part - comp;
-                const float t = sum + y;
-                comp = (t - sum) - y;
-                sum = t;
             }
         }
         if (!COUNT && active) {

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kRingChunk = 64;
-constexpr double kPi = 3.14159265358979323846;
+
 
 struct SymRing {  // shared-memory constants of one (output ring, input ring) pair
     DF A, B, c;
@@ -59,25 +59,12 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int k, bool a
         if (tid < nq) {
             const int q = q0 + tid;
             const DevRing Qr = P.d_rings[q];
-            const double dz = R.z - Qr.z;
-            const double ds = (Qr.z - R.z) * (Qr.z + R.z) / (R.s + Qr.s);
-            const double A = dz * dz + ds * ds;
-            const double ss = R.s * Qr.s;
-            float hw;
-            if (skip_belt_inputs && q >= P.belt_lo && q <= P.belt_hi) {
-                hw = -1.0f;
-            } else if (A > (double)P.dc2 * (1.0 + 1e-6)) {
-                hw = -1.0f;
-            } else {
-                const double cdp = (P.cos_cut - R.z * Qr.z) / ss;
-                double dphi = cdp <= -1.0 ? 4.0 * kPi : (cdp >= 1.0 ? 0.0 : acos(cdp));
-                hw = (float)(dphi * Qr.len / (2.0 * kPi)) + 1.0f;
-            }
+            const PairInfo pi = P.d_pairs[P.d_pair_base[r] + (q - rg.x)];
             SymRing g;
-            g.A = df_from_double(A * P.scale2);
-            g.B = df_from_double(4.0 * ss * P.scale2);
-            g.c = df_from_double(kPi / (2.0 * (double)L * (double)Qr.len));
-            g.hw = hw;
+            g.A = DF{pi.Ah, pi.Al};
+            g.B = DF{pi.Bh, pi.Bl};
+            g.c = DF{pi.ch, pi.cl};
+            g.hw = (skip_belt_inputs && q >= P.belt_lo && q <= P.belt_hi) ? -1.0f : pi.hw;
             g.len = Qr.len;
             g.start = Qr.start;
             g.start_m = P.d_rings[P.nrings - 1 - q].start;
@@ -105,42 +92,48 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int k, bool a
             if (idb < 0) idb += L2;
             const float *mn = m + g.start;
             const float *ms = m + g.start_m;
-            float part[2 * NI];
+            // blocks of 32 window steps: FP32 partial sums, Kahan-folded into
+            // the totals after each block
+            for (int kb0 = klo; kb0 <= khi; kb0 += 32) {
+                const int kend = min(kb0 + 31, khi);
+                float part[2 * NI];
 #pragma unroll
-            for (int i = 0; i < 2 * NI; ++i) part[i] = 0.0f;
-            for (int kk = klo; kk <= khi; ++kk) {
-                const float xh = Nf * g.c.h;
-                const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
-                int ti;
-                float f;
-                if (chord_to_table(g.A, g.B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f)) {
-                    const float w = hermite(__ldg(&P.d_tab[ti]), f);
-                    int j = idx, jb = idb;
+                for (int i = 0; i < 2 * NI; ++i) part[i] = 0.0f;
+                for (int kk = kb0; kk <= kend; ++kk) {
+                    const float xh = Nf * g.c.h;
+                    const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
+                    int ti;
+                    float f;
+                    if (chord_to_table(g.A, g.B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f)) {
+                        const float w = hermite(__ldg(&P.d_tab[ti]), f);
+                        int j = idx, jb = idb;
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        part[qq] = fmaf(w, __ldg(mn + j), part[qq]);
-                        if constexpr (MIRROR) part[4 + qq] = fmaf(w, __ldg(ms + j), part[4 + qq]);
-                        if (refl) {
-                            part[NI + qq] = fmaf(w, __ldg(mn + jb), part[NI + qq]);
+                        for (int qq = 0; qq < 4; ++qq) {
+                            part[qq] = fmaf(w, __ldg(mn + j), part[qq]);
                             if constexpr (MIRROR)
-                                part[NI + 4 + qq] = fmaf(w, __ldg(ms + jb), part[NI + 4 + qq]);
+                                part[4 + qq] = fmaf(w, __ldg(ms + j), part[4 + qq]);
+                            if (refl) {
+                                part[NI + qq] = fmaf(w, __ldg(mn + jb), part[NI + qq]);
+                                if constexpr (MIRROR)
+                                    part[NI + 4 + qq] = fmaf(w, __ldg(ms + jb), part[NI + 4 + qq]);
+                            }
+                            j += Q2;
+                            if (j >= L2) j -= L2;
+                            jb += Q2;
+                            if (jb >= L2) jb -= L2;
                         }
-                        j += Q2;
-                        if (j >= L2) j -= L2;
-                        jb += Q2;
-                        if (jb >= L2) jb -= L2;
                     }
+                    Nf -= step;
+                    if (++idx == L2) idx = 0;
+                    if (--idb < 0) idb = L2 - 1;
                 }
-                Nf -= step;
-                if (++idx == L2) idx = 0;
-                if (--idb < 0) idb = L2 - 1;
-            }
 #pragma unroll
-            for (int i = 0; i < 2 * NI; ++i) {
-                const float y = part[i] - comp[i];
-                const float tt = sum[i] + y;
-                comp[i] = (tt - sum[i]) - y;
-                sum[i] = tt;
+                for (int i = 0; i < 2 * NI; ++i) {
+                    const float y = part[i] - comp[i];
+                    const float tt = sum[i] + y;
+                    comp[i] = (tt - sum[i]) - y;
+                    sum[i] = tt;
+                }
             }
         }
     }

@@ -25,21 +25,33 @@ __host__ __device__ inline DF df_from_double(double v) {
     return r;
 }
 
-// sin(x) for x = xh + xl, |x| <= pi/2 + small, as a pair (xh, lo): the leading
-// term x is carried exactly and only the Taylor tail x^3 (-1/3! + x^2/5! - ...)
-// (to x^13) and the xl cos(x) correction are rounded.
+// sin(x) for x = xh + xl, |x| <= pi/2 + small, as a normalised pair
+// (|lo| <= ulp(hi), as chord_to_table assumes).  sin x = x - x^3/6 + x^5 q(x^2)
+// with q the Taylor series to x^13: x (exact) and -x^3/6 are carried in
+// double-float, the smaller x^5 q term and the xl cos(x) correction in FP32.
 __device__ __forceinline__ DF sin_df(float xh, float xl) {
-    const float x2 = xh * xh;
-    float q = 1.6059043836821613e-10f;         //  1/13!
-    q = fmaf(q, x2, -2.5052108385441720e-08f); // -1/11!
-    q = fmaf(q, x2, 2.7557319223985893e-06f);  //  1/9!
-    q = fmaf(q, x2, -1.9841269841269841e-04f); // -1/7!
-    q = fmaf(q, x2, 8.3333333333333333e-03f);  //  1/5!
-    q = fmaf(q, x2, -1.6666666666666667e-01f); // -1/3!
-    const float c = fmaf(x2, fmaf(x2, 4.1666666666666664e-02f, -0.5f), 1.0f);  // ~cos
+    const float x2h = xh * xh;
+    const float x2l = fmaf(xh, xh, -x2h);               // x^2 = x2h + x2l exactly
+    const float x3h = xh * x2h;
+    const float x3l = fmaf(xh, x2h, -x3h) + xh * x2l;    // x^3
+    const float c6h = -0.16666667163372040f;             // -1/6 = c6h + c6l
+    const float c6l = 4.9670538793415e-09f;
+    const float t1h = x3h * c6h;
+    const float t1l = fmaf(x3h, c6h, -t1h) + fmaf(x3h, c6l, x3l * c6h);  // -x^3/6
+    float q = fmaf(1.6059043836821613e-10f, x2h, -2.5052108385441720e-08f);  // 1/13!, -1/11!
+    q = fmaf(q, x2h, 2.7557319223985893e-06f);           //  1/9!
+    q = fmaf(q, x2h, -1.9841269841269841e-04f);          // -1/7!
+    q = fmaf(q, x2h, 8.3333333333333333e-03f);           //  1/5!
+    const float rest = (x3h * x2h) * q;                  // x^5 q(x^2)
+    const float c = fmaf(x2h, fmaf(x2h, 4.1666666666666664e-02f, -0.5f), 1.0f);  // ~cos
+    // two-sum of the high parts, then normalise
+    const float sh = xh + t1h;
+    const float bp = sh - xh;
+    const float e = (xh - (sh - bp)) + (t1h - bp);
+    const float sl = e + t1l + rest + xl * c;
     DF s;
-    s.h = xh;
-    s.l = fmaf(xh * x2, q, xl * c);
+    s.h = sh + sl;
+    s.l = (sh - s.h) + sl;
     return s;
 }
 

@@ -26,6 +26,18 @@ struct DevRing {
     int len, start, phase, pad;
 };
 
+// Geometry of one (output ring r, input ring q) pair, computed once per split
+// on the host in FP64.  In table-position units (chord * n_int / chord_cut):
+// u^2 = A + B sin^2(x), x = N * c with N the exact pixel-pair integer; hw is
+// the half window in input pixels (dphi_max L_q / 2 pi + 1), negative when no
+// pixel of q lies within theta_cut; w = ceil(dphi_max L_q / 2 pi) + 1 is the
+// integer half window of the circulant belt kernel.
+struct PairInfo {
+    float Ah, Al, Bh, Bl, ch, cl;
+    float hw;
+    int w;
+};
+
 // ---------------------------------------------------------------------------
 // Host FP64 split fit (Sec. 2, Eq. 1-6).
 // ---------------------------------------------------------------------------
@@ -68,6 +80,8 @@ struct ConvPlan {
     int nside, npix, nrings;
     const DevRing *d_rings;  // nrings
     const int2 *d_range;     // per output ring: first/last input ring (0-based)
+    const PairInfo *d_pairs; // ring-pair geometry, d_pair_base[r] + (q - range.x)
+    const int *d_pair_base;
     const float4 *d_tab;     // table
     int n_int;
     float inv_h;             // 1 / interval width
@@ -76,6 +90,7 @@ struct ConvPlan {
     float domega;            // 4 pi / Npix
     int belt_lo, belt_hi;    // 0-based ring indices of the equatorial belt
     double scale2;           // (n_int / chord_cut)^2: chord^2 -> table position^2
+    float belt_c1h, belt_c1l; // pi / (2 L_belt) as a double-float pair
     float nint2;             // the cut in table-position^2 units (n_int^2)
 };
 // General ring-pair gather.  With belt_split set, belt output rings only take
@@ -106,6 +121,9 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
                             long long map_stride, int belt_split, int band_lo,
                             int band_hi, cudaStream_t st);
 
+// Record the message returned by ksc_last_error() on this thread.
+void set_last_error(const std::string &msg);
+
 // Largest table (intervals) a convolution kernel keeps in shared memory.
 constexpr int kMaxIntervals = 8192;
 
@@ -124,6 +142,8 @@ struct ksc_split {
     float4 *d_tab = nullptr;
     ksc::DevRing *d_rings = nullptr;
     int2 *d_range = nullptr;
+    ksc::PairInfo *d_pairs = nullptr;
+    int *d_pair_base = nullptr;
     // work lists, each with a per-ring prefix (nrings + 1 offsets)
     ksc::WorkItem *d_items = nullptr;   // every ring (pair counting)
     int n_items = 0;

@@ -111,6 +111,14 @@ def _dptr(t):
     return t.data_ptr()
 
 
+def _dptr_typed(t, dtype_name: str):
+    """Device address of a contiguous CUDA tensor of the given dtype."""
+    import torch
+    if not t.is_cuda or t.dtype != getattr(torch, dtype_name) or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype_name} CUDA tensor")
+    return t.data_ptr()
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -263,3 +271,4 @@ def conv_real_host(s: Split, h_in, h_out=None):
     _check(_lib.ksc_conv_real_host(s.handle, h_in.data_ptr(), ho.data_ptr()),
            "ksc_conv_real_host")
     return ho
+
