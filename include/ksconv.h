@@ -196,6 +196,26 @@ int ksc_count_pairs(ksc_split *s, long long *n_pairs);
  */
 int ksc_device_status(const ksc_split *s, void *stream);
 
+/*
+ * Allocation-free table build (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory where they need a table, such as
+ * code under a caching allocator or a fixed memory budget that owns all
+ * device memory, real-time loops that cannot afford cudaMalloc's implicit
+ * synchronisation, or work issued during CUDA stream capture).
+ * Builds the same K_r table as ksc_make_split_real (see ksc_split_table for
+ * the layout): d_c = lmax+1 real-space Legendre coefficients (device, FP64),
+ * d_table = n_intervals * 4 floats (device, 16-byte aligned), both owned by
+ * the caller.  Asynchronous on `stream`; calls no allocator.  Its node scratch
+ * is a built-in device array sized for n_intervals <= 8192 (131 kB held on
+ * every device that loads the library until exit); larger n_intervals is
+ * rejected with KSC_ERR_ARG.  Calls share that array: calls that overlap on
+ * the GPU race.  The first call on each device looks up the array's address
+ * (not allowed during stream capture): make it before any capture.
+ * Errors: KSC_ERR_ARG, KSC_ERR_CUDA, KSC_ERR_UNSUPPORTED (device index > 63).
+ */
+int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
+                            int n_intervals, float *d_table, void *stream);
+
 /* Release a split and its device memory (NULL is a no-op). */
 void ksc_free_split(ksc_split *s);
 

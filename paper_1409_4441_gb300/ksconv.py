@@ -37,7 +37,7 @@ EXPORTS = [
     "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
     "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
     "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_count_pairs", "ksc_device_status",
-    "ksc_free_split",
+    "ksc_free_split", "ksc_build_table_noalloc",
     "ksc_status_string", "ksc_last_error",
 ]
 
@@ -77,6 +77,7 @@ _sig = {
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
+    "ksc_build_table_noalloc": [_vp, _i, _d, _i, _vp, _vp],
     "ksc_status_string": [_i],
     "ksc_last_error": [],
 }
@@ -272,3 +273,13 @@ def conv_real_host(s: Split, h_in, h_out=None):
            "ksc_conv_real_host")
     return ho
 
+
+def build_table_noalloc(d_c, lmax: int, theta_cut: float, n_intervals: int, d_table,
+                        stream=None):
+    """ksc_build_table_noalloc: the K_r table from device coefficients d_c
+    (float64, lmax+1) into d_table (float32, n_intervals x 4), without any
+    device allocation (for callers that cannot allocate; see ksconv.h)."""
+    _check(_lib.ksc_build_table_noalloc(_dptr_typed(d_c, "float64"), lmax, float(theta_cut),
+                                        n_intervals, _dptr_typed(d_table, "float32"),
+                                        _stream(stream)), "ksc_build_table_noalloc")
+    return d_table
