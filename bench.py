@@ -30,7 +30,14 @@ sys.path.insert(0, ROOT)
 from paper_1409_4441_gb300 import inputs  # noqa: E402
 
 ARC = inputs.ARCMIN
-WORKLOAD = dict(nside=2048, lmax=4096, fwhm=5.0 * ARC, lcut=1024, theta_cut=240.0 * ARC)
+WORKLOADS = {
+    # the Planck-resolution case (Sec. 2-3 sizes): the benchmark line
+    "nside2048": dict(nside=2048, lmax=4096, fwhm=5.0 * ARC, lcut=1024, theta_cut=240.0 * ARC),
+    # the same per-ring-pair shape at a quarter of the resolution (every angle x4),
+    # small enough for full ncu captures
+    "nside512": dict(nside=512, lmax=1024, fwhm=20.0 * ARC, lcut=256, theta_cut=960.0 * ARC),
+}
+WORKLOAD = dict(WORKLOADS["nside2048"])
 METRIC = "pixel-pair interactions/s and maps/s at nside=2048 vs roofline, at 1e-5 C_l rms err"
 UNIT = "pairs/s"
 N_SM = 152
@@ -38,12 +45,15 @@ FP32_LANES_PER_SM = 128
 
 
 def workload_desc(extra=None):
-    d = {"workload": "nside-2048 real-space convolution: 50.3M-pixel FP32 map, l_max 4096, "
-                     "5' Gaussian beam, least-squares split l_cut 1024, theta_cut 240', "
-                     "white-noise input",
-         "nside": WORKLOAD["nside"], "lmax": WORKLOAD["lmax"], "fwhm_arcmin": 5.0,
-         "l_cut": WORKLOAD["lcut"], "theta_cut_arcmin": 240.0,
-         "l2": "inputs larger than L2 (201 MB map in, 201 MB out)"}
+    W = WORKLOAD
+    npix = 12 * W["nside"] ** 2
+    d = {"workload": f"nside-{W['nside']} real-space convolution: {npix / 1e6:.1f}M-pixel FP32 map, "
+                     f"l_max {W['lmax']}, {W['fwhm'] / ARC:.0f}' Gaussian beam, least-squares split "
+                     f"l_cut {W['lcut']}, theta_cut {W['theta_cut'] / ARC:.0f}', white-noise input",
+         "nside": W["nside"], "lmax": W["lmax"], "fwhm_arcmin": W["fwhm"] / ARC,
+         "l_cut": W["lcut"], "theta_cut_arcmin": W["theta_cut"] / ARC,
+         "l2": ("inputs larger than L2 (201 MB map in, 201 MB out)" if npix * 4 > 129e6
+                else "inputs smaller than L2 (profiling case)")}
     if extra:
         d.update(extra)
     return d
@@ -148,7 +158,10 @@ def run_reference(args, world, rank):
     nside = WORKLOAD["nside"]
     m64 = inputs.white_noise_map(nside, inputs.seed_for(3)).astype(np.float32).astype(np.float64)
     c = sharp_coeffs()
-    n_int = 4368  # the library's automatic table size for this workload
+    # the library's automatic table size (about 96 intervals per shortest l_max wavelength)
+    dc = 2.0 * np.sin(0.5 * WORKLOAD["theta_cut"])
+    n_int = int(min(8192, max(256, np.ceil(96.0 * dc * WORKLOAD["lmax"] /
+                                           (2 * np.pi * np.cos(0.5 * WORKLOAD["theta_cut"]))))))
     n_pix = args.ref_pixels
     cores = os.cpu_count()
     for w in range(args.warmup):
@@ -159,7 +172,7 @@ def run_reference(args, world, rank):
         tot_pairs += p
         tot_t += t
     v = tot_pairs / tot_t
-    sample = f"{args.steps} steps x {n_pix} random output pixels of the nside-2048 map"
+    sample = f"{args.steps} steps x {n_pix} random output pixels of the nside-{nside} map"
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
@@ -289,7 +302,7 @@ def run_ours(args, world, rank, local):
             oracle_sample(16, 5, c, info["n_intervals"], m64)
             p, t = oracle_sample(args.cpu_pixels, 6, c, info["n_intervals"], m64)
             cpu = {"value": p / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": f"{args.cpu_pixels} random output pixels of the nside-2048 map, "
+                   "sample": f"{args.cpu_pixels} random output pixels of the nside-{nside} map, "
                              f"all-pairs FP64 brute force ({t:.1f} s)"}
         except Exception as e:  # the baseline must not sink the GPU number
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -331,7 +344,10 @@ def main():
     ap.add_argument("--cpu-pixels", type=int, default=512)
     ap.add_argument("--ref-pixels", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="nside2048", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
