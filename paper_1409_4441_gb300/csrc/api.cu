@@ -214,11 +214,11 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         cudaFree(d_c);
         return cuda_fail(e, "allocate table nodes");
     }
-    if ((e = cudaMalloc(&s->d_tab, sizeof(float4) * n_int)) != cudaSuccess) {
+    if ((e = cudaMalloc(&s->d_tab, sizeof(float4) * (n_int + 1))) != cudaSuccess) {
         cudaFree(d_c); cudaFree(d_nodes);
         return cuda_fail(e, "allocate table");
     }
-    ksc::TableBuild tb{d_c, s->lmax, n_int, s->chord_cut / n_int, s->d_tab, d_nodes};
+    ksc::TableBuild tb{d_c, s->lmax, n_int, s->chord_cut / n_int, s->d_tab, d_nodes, 1};
     e = ksc::launch_table_build(tb, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     cudaFree(d_c);

@@ -15,43 +15,138 @@
 // One thread owns one reflection class {k, kb} of first-quarter positions of
 // a northern ring (a class of one when kb coincides with k up to a quarter
 // turn) and produces all its images (no mirror on the equator ring, which is
-// its own mirror image).  The chord and table position are computed in
-// double-float from FP64 ring-pair constants and the exact integer
-// N = (2k + t) L' - (2k' + t') L with dphi / 2 = N pi / (2 L L')
-// (ksc_device.cuh); K_r comes from the cubic Hermite table through the L1
-// cache.  Each input ring's FP32 partial sums are Kahan-folded into totals.
+// its own mirror image).  Per input ring the CTA stages, for the union of its
+// threads' windows, the sixteen image sequences m[image(k')] in shared memory
+// so that every image of input position k' sits at the same offset; each
+// thread then walks its window four positions at a time: four independent
+// kernel evaluations, then one 16-byte shared load per image feeding four
+// FFMAs.  Chord and table position are computed in double-float from the
+// ring-pair table and the exact integer N = (2k + t) L' - (2k' + t') L,
+// dphi / 2 = N pi / (2 L L') (ksc_device.cuh); K_r comes from the cubic
+// Hermite table through the L1 cache.  FP32 partial sums over 32 positions are
+// Kahan-folded into the totals.
 #include "ksc_device.cuh"
 #include "ksc_internal.h"
 
 namespace ksc {
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kRingChunk = 64;
+constexpr int kThreads = 128;   // one thread per reflection class
+constexpr int kRingChunk = 32;  // ring-pair constants staged per pass
+constexpr int kSpan = 512;      // staged input positions per segment
+constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, reflected}
+constexpr int kStride = kSpan + 4;
 
-
-struct SymRing {  // shared-memory constants of one (output ring, input ring) pair
+struct SymRing {  // one (output ring, input ring) pair
     DF A, B, c;
     float hw;
-    int len, start, start_m, phase;
+    int len, start, start_m, phase, small;
 };
 
+__device__ __forceinline__ int pmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// Window [klo, khi] of input positions for output class k (one pixel of margin
+// around |dphi| <= dphi_max; the whole ring, once, when a partial window could
+// reach the ring's length).  The choice depends on the ring pair only, so both
+// ends are nondecreasing in k and the CTA's union of windows runs from the
+// first class's klo to the last class's khi.
+__device__ __forceinline__ void window(int k, int t, int L, const SymRing &g, long long *num,
+                                       int *klo, int *khi) {
+    const int L2 = g.len;
+    *num = (long long)(2 * k + t) * L2 - (long long)g.phase * L;
+    const float kc = (float)*num / (float)(2 * L);
+    int lo, hi;
+    if (2.0f * g.hw + 3.0f >= (float)L2) {
+        lo = (int)floorf(kc) - L2 / 2;
+        hi = lo + L2 - 1;
+    } else {
+        lo = (int)floorf(kc - g.hw);
+        hi = (int)ceilf(kc + g.hw);  // hi - lo + 1 <= 2 hw + 3 < L2
+    }
+    *klo = lo;
+    *khi = hi;
+}
+
+__device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
+    const float y = v - *comp;
+    const float tt = *sum + y;
+    *comp = (tt - *sum) - y;
+    *sum = tt;
+}
+
+// Positions a..b of one staged segment (starting at s0) for one thread.
+template <bool MIRROR, bool SMALL>
+__device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float *st,
+                                           int s0, int a, int b, long long num, int L, bool refl,
+                                           float *sum, float *comp) {
+    const float step = (float)(2 * L);
+    float part[kImg];
+#pragma unroll
+    for (int i = 0; i < kImg; ++i) part[i] = 0.0f;
+    int nq = 0;
+    for (int kq = s0 + ((a - s0) & ~3); kq <= b; kq += 4) {
+        const float N0 = (float)(num - 2LL * kq * L);  // exact integer below 2^24
+        float w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float Nf = N0 - (float)e * step;
+            const float xh = Nf * g.c.h;
+            const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
+            const DF sn = SMALL ? sin_df_small(xh, xl) : sin_df(xh, xl);
+            const int kp = kq + e;
+            int ti;
+            float f;
+            w[e] = 0.0f;
+            if (kp >= a && kp <= b && chord_to_table_padded(g.A, g.B, sn, P.nint2, &ti, &f))
+                w[e] = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
+        }
+        const int j = kq - s0;
+#pragma unroll
+        for (int img = 0; img < kImg; ++img) {
+            if (!MIRROR && (img & 4)) continue;
+            if (img >= 8 && !refl) continue;
+            const float4 v = *reinterpret_cast<const float4 *>(st + img * kStride + j);
+            float p = part[img];
+            p = fmaf(w[0], v.x, p);
+            p = fmaf(w[1], v.y, p);
+            p = fmaf(w[2], v.z, p);
+            p = fmaf(w[3], v.w, p);
+            part[img] = p;
+        }
+        if (++nq == 8) {  // fold every 32 positions
+            nq = 0;
+#pragma unroll
+            for (int i = 0; i < kImg; ++i) {
+                kahan(&sum[i], &comp[i], part[i]);
+                part[i] = 0.0f;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kImg; ++i) kahan(&sum[i], &comp[i], part[i]);
+}
+
 template <bool MIRROR>
-__device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int k, bool active,
+__device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n_cls,
                                          bool skip_belt_inputs, bool add, int band_lo,
                                          int band_hi, const float *__restrict__ m,
-                                         float *__restrict__ o, SymRing *sR) {
+                                         float *__restrict__ o, SymRing *sR, float *st) {
     const int tid = threadIdx.x;
     const DevRing R = P.d_rings[r];
     const int L = R.len, Q = L / 4, t = R.phase;
     const int2 rg = P.d_range[r];
+    const int k = c0 + tid;
+    const bool active = k < n_cls;
+    const int k_first = c0, k_last = min(c0 + kThreads, n_cls) - 1;
     // reflection partner of k; none when it is k itself up to a quarter turn
     const int kb = Q - k - t;
     const bool refl = kb != k && kb != Q;
-    constexpr int NI = MIRROR ? 8 : 4;  // images per class member
-    float sum[2 * NI], comp[2 * NI];
+    float sum[kImg], comp[kImg];
 #pragma unroll
-    for (int i = 0; i < 2 * NI; ++i) sum[i] = comp[i] = 0.0f;
+    for (int i = 0; i < kImg; ++i) sum[i] = comp[i] = 0.0f;
 
     for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
         const int nq = min(kRingChunk, rg.y - q0 + 1);
@@ -69,71 +164,49 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int k, bool a
             g.start = Qr.start;
             g.start_m = P.d_rings[P.nrings - 1 - q].start;
             g.phase = Qr.phase;
+            // |dphi / 2| < 0.25 over the whole (partial) window: the cheap sine
+            g.small = (2.0f * pi.hw + 3.0f < (float)Qr.len) &&
+                      ((pi.hw + 1.0f) * 3.14159265f / (float)Qr.len < 0.25f);
             sR[tid] = g;
         }
         __syncthreads();
-        if (!active) continue;
         for (int qi = 0; qi < nq; ++qi) {
             const SymRing g = sR[qi];
             if (g.hw < 0.0f) continue;
             const int L2 = g.len, Q2 = L2 / 4;
-            const long long num = (long long)(2 * k + t) * L2 - (long long)g.phase * L;
-            const float kc = (float)num / (float)(2 * L);
-            int klo = (int)floorf(kc - g.hw), khi = (int)ceilf(kc + g.hw);
-            if (2.0f * g.hw + 1.0f >= (float)L2 || khi - klo + 1 >= L2) {
-                klo = (int)floorf(kc) - L2 / 2;
-                khi = klo + L2 - 1;
-            }
-            float Nf = (float)(num - 2LL * klo * L);  // exact integer below 2^24
-            const float step = (float)(2 * L);
-            int idx = klo % L2;               // k' mod L2
-            if (idx < 0) idx += L2;
-            int idb = (Q2 - klo - g.phase) % L2;  // (Q2 - k' - t') mod L2
-            if (idb < 0) idb += L2;
-            const float *mn = m + g.start;
-            const float *ms = m + g.start_m;
-            // blocks of 32 window steps: FP32 partial sums, Kahan-folded into
-            // the totals after each block
-            for (int kb0 = klo; kb0 <= khi; kb0 += 32) {
-                const int kend = min(kb0 + 31, khi);
-                float part[2 * NI];
+            long long num, numx;
+            int klo, khi, U0, U1, dummy;
+            window(k, t, L, g, &num, &klo, &khi);
+            window(k_first, t, L, g, &numx, &U0, &dummy);
+            window(k_last, t, L, g, &numx, &dummy, &U1);
+            for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
+                __syncthreads();  // the previous segment is consumed
+                for (int j = tid; j < kSpan; j += kThreads) {
+                    const int kp = s0 + j;
+                    const int idx = pmod(kp, L2);
+                    const int idr = pmod(Q2 - kp - g.phase, L2);
 #pragma unroll
-                for (int i = 0; i < 2 * NI; ++i) part[i] = 0.0f;
-                for (int kk = kb0; kk <= kend; ++kk) {
-                    const float xh = Nf * g.c.h;
-                    const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
-                    int ti;
-                    float f;
-                    if (chord_to_table(g.A, g.B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f)) {
-                        const float w = hermite(__ldg(&P.d_tab[ti]), f);
-                        int j = idx, jb = idb;
-#pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            part[qq] = fmaf(w, __ldg(mn + j), part[qq]);
-                            if constexpr (MIRROR)
-                                part[4 + qq] = fmaf(w, __ldg(ms + j), part[4 + qq]);
-                            if (refl) {
-                                part[NI + qq] = fmaf(w, __ldg(mn + jb), part[NI + qq]);
-                                if constexpr (MIRROR)
-                                    part[NI + 4 + qq] = fmaf(w, __ldg(ms + jb), part[NI + 4 + qq]);
-                            }
-                            j += Q2;
-                            if (j >= L2) j -= L2;
-                            jb += Q2;
-                            if (jb >= L2) jb -= L2;
+                    for (int qq = 0; qq < 4; ++qq) {
+                        int ia = idx + qq * Q2;
+                        if (ia >= L2) ia -= L2;
+                        int ib = idr + qq * Q2;
+                        if (ib >= L2) ib -= L2;
+                        st[qq * kStride + j] = __ldg(m + g.start + ia);
+                        st[(8 + qq) * kStride + j] = __ldg(m + g.start + ib);
+                        if constexpr (MIRROR) {
+                            st[(4 + qq) * kStride + j] = __ldg(m + g.start_m + ia);
+                            st[(12 + qq) * kStride + j] = __ldg(m + g.start_m + ib);
                         }
                     }
-                    Nf -= step;
-                    if (++idx == L2) idx = 0;
-                    if (--idb < 0) idb = L2 - 1;
                 }
-#pragma unroll
-                for (int i = 0; i < 2 * NI; ++i) {
-                    const float y = part[i] - comp[i];
-                    const float tt = sum[i] + y;
-                    comp[i] = (tt - sum[i]) - y;
-                    sum[i] = tt;
-                }
+                __syncthreads();
+                if (!active) continue;
+                const int a = max(klo, s0), b = min(khi, s0 + kSpan - 1);
+                if (a > b) continue;
+                if (g.small)
+                    accumulate<MIRROR, true>(P, g, st, s0, a, b, num, L, refl, sum, comp);
+                else
+                    accumulate<MIRROR, false>(P, g, st, s0, a, b, num, L, refl, sum, comp);
             }
         }
     }
@@ -149,13 +222,13 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int k, bool a
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int kq = kk + qq * Q;
-                const float vn = sum[c * NI + qq] * P.domega;
+                const float vn = sum[8 * c + qq] * P.domega;
                 if (wn) {
                     if (add) o[R.start + kq] += vn;
                     else o[R.start + kq] = vn;
                 }
                 if constexpr (MIRROR) {
-                    const float vs = sum[c * NI + 4 + qq] * P.domega;
+                    const float vs = sum[8 * c + 4 + qq] * P.domega;
                     if (ws) {
                         if (add) o[start_s + kq] += vs;
                         else o[start_s + kq] = vs;
@@ -166,11 +239,12 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int k, bool a
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
                 int belt_split, int band_lo, int band_hi) {
     __shared__ SymRing sR[kRingChunk];
+    __shared__ __align__(16) float st[kImg * kStride];
     const float *m = in + (long long)blockIdx.y * map_stride;
     float *o = out + (long long)blockIdx.y * map_stride;
     const int eq = (P.nrings - 1) / 2;  // the equator ring, its own mirror image
@@ -179,14 +253,12 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
         const DevRing R = P.d_rings[w.ring];
         const int Q = R.len / 4;
         const int n_cls = R.phase ? (Q + 1) / 2 : Q / 2 + 1;  // reflection classes
-        const int k = w.k0 + threadIdx.x;
-        const bool active = k < n_cls;
         const bool belt = w.ring >= P.belt_lo && w.ring <= P.belt_hi;
         const bool add = belt_split && belt;
         if (w.ring == eq)
-            sym_item<false>(P, w.ring, k, active, add, add, band_lo, band_hi, m, o, sR);
+            sym_item<false>(P, w.ring, w.k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
         else
-            sym_item<true>(P, w.ring, k, active, add, add, band_lo, band_hi, m, o, sR);
+            sym_item<true>(P, w.ring, w.k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
     }
 }
 

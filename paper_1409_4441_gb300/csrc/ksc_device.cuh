@@ -89,6 +89,43 @@ __device__ __forceinline__ bool chord_to_table(DF A, DF B, DF s, float nint2, in
     return true;
 }
 
+// sin(x) as a normalised pair for |x| < 0.25: the Taylor tail x^3 q(x^2) (to
+// x^9) in FP32 is below 2e-9 of sin x on this range, and cos x ~ 1 is enough
+// for the xl correction.
+__device__ __forceinline__ DF sin_df_small(float xh, float xl) {
+    const float x2 = xh * xh;
+    float q = fmaf(2.7557319223985893e-06f, x2, -1.9841269841269841e-04f);  //  1/9!, -1/7!
+    q = fmaf(q, x2, 8.3333333333333333e-03f);                                //  1/5!
+    q = fmaf(q, x2, -1.6666666666666667e-01f);                               // -1/3!
+    const float tail = fmaf(xh * x2, q, xl);
+    DF s;
+    s.h = xh + tail;
+    s.l = (xh - s.h) + tail;
+    return s;
+}
+
+// chord_to_table for a table padded with an entry at n_int (the cut itself,
+// u <= n_int, then needs no index clamp; u >= 0 always).
+__device__ __forceinline__ bool chord_to_table_padded(DF A, DF B, DF s, float nint2, int *i_out,
+                                                      float *f_out) {
+    const float s2h = s.h * s.h;
+    const float s2l = fmaf(2.0f * s.h, s.l, fmaf(s.h, s.h, -s2h));
+    const float ph = B.h * s2h;
+    const float pl = fmaf(B.h, s2h, -ph) + fmaf(B.h, s2l, B.l * s2h);
+    const float dh = A.h + ph;
+    const float bp = dh - A.h;
+    const float e = (A.h - (dh - bp)) + (ph - bp);
+    const float dl = e + A.l + pl;
+    if (dh > nint2) return false;
+    const float r = rsqrtf(fmaxf(dh, 1e-30f));
+    const float uh = dh * r;
+    const float ul = (fmaf(-uh, uh, dh) + dl) * (0.5f * r);
+    const float t = (uh - 0.5f) + 12582912.0f;
+    *i_out = __float_as_int(t) - 0x4B400000;
+    *f_out = (uh - (t - 12582912.0f)) + ul;
+    return true;
+}
+
 __device__ __forceinline__ float hermite(const float4 c, float f) {
     return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
 }

@@ -65,8 +65,10 @@ struct TableBuild {
     int lmax;
     int n_int;
     double h;           // chord spacing
-    float4 *d_tab;      // n_int intervals (output)
+    float4 *d_tab;      // n_int intervals (output; n_int + 1 entries when pad is set)
     double *d_nodes;    // 2*(n_int+1) scratch: node values, node slopes
+    int pad = 0;        // also write entry n_int: the constant-slope extension past d_cut,
+                        // so that table position u = n_int needs no index clamp
 };
 cudaError_t launch_table_build(const TableBuild &tb, cudaStream_t st);
 

@@ -44,8 +44,12 @@ __global__ void node_values_kernel(const double *__restrict__ c, int lmax, int n
 
 __global__ void hermite_coeff_kernel(const double *__restrict__ nodeK,
                                      const double *__restrict__ nodeD, int n_int, double h,
-                                     float4 *__restrict__ tab) {
+                                     int pad, float4 *__restrict__ tab) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pad && k == n_int) {
+        tab[k] = make_float4((float)nodeK[k], (float)(h * nodeD[k]), 0.0f, 0.0f);
+        return;
+    }
     if (k >= n_int) return;
     const double y0 = nodeK[k], y1 = nodeK[k + 1];
     const double m0 = h * nodeD[k], m1 = h * nodeD[k + 1];
@@ -64,8 +68,8 @@ cudaError_t launch_table_build(const TableBuild &tb, cudaStream_t st) {
     double *nodeK = tb.d_nodes, *nodeD = tb.d_nodes + n_nodes;
     node_values_kernel<<<(n_nodes + 127) / 128, 128, 0, st>>>(tb.d_c, tb.lmax, n_nodes, tb.h,
                                                              nodeK, nodeD);
-    hermite_coeff_kernel<<<(tb.n_int + 255) / 256, 256, 0, st>>>(nodeK, nodeD, tb.n_int, tb.h,
-                                                               tb.d_tab);
+    hermite_coeff_kernel<<<(tb.n_int + 1 + 255) / 256, 256, 0, st>>>(nodeK, nodeD, tb.n_int,
+                                                                   tb.h, tb.pad, tb.d_tab);
     return cudaGetLastError();
 }
 
