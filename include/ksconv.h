@@ -73,6 +73,9 @@ typedef struct {
                           wavelength, at most 8192)                             */
     int path;          /* 0 (default): circulant belt kernel + symmetric gather;
                           1: general ring-pair gather only (reference path)   */
+    int tensor;        /* 0 (default): ksc_conv_real_multimap runs belt ring
+                          pairs on the tcgen05 tensor cores (TF32 x3, FP32
+                          accumulate) when n_maps >= 16; 1: FFMA kernels only */
 } ksc_split_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -182,6 +185,13 @@ int ksc_conv_real_host(const ksc_split *s, const float *h_in, float *h_out);
  */
 int ksc_conv_real_stage(const ksc_split *s, const float *d_in, float *d_out,
                         int stage, void *stream);
+
+/* The same two stages for a stack of n_maps maps ([n_maps][Npix] device
+ * arrays); stage 1 uses the tensor kernel under the same rule as
+ * ksc_conv_real_multimap.  Stage 1 then stage 2 equals that call bit for bit. */
+int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in,
+                                 float *d_out, int n_maps, int stage,
+                                 void *stream);
 
 /* Count ordered in-disc pixel pairs on the device (synchronous); also stored
  * in the split (with the belt-belt subset) and reported by ksc_split_info. */

@@ -46,6 +46,7 @@ void release(ksc_split *s) {
     cudaFree(s->d_pair_base);
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
+    cudaFree(s->d_items_mma);
     cudaFree(s->d_items_belt);
     cudaFree(s->d_err);
     cudaFree(s->d_io);
@@ -128,6 +129,14 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
             }
         }
     }
+    std::vector<int2> items_mma;
+    for (int r = belt_lo; r <= belt_hi; ++r)
+        for (int k0 = 0; k0 < g.len[r]; k0 += ksc::belt_mma_block())
+            items_mma.push_back(make_int2(r, k0));
+    s->n_items_mma = (int)items_mma.size();
+    s->w_cap = (max_nd + 2 * 13 + 3) & ~3;
+    s->tensor = o.tensor;
+    if (ksc::belt_mma_smem(s->w_cap) > 220u * 1024) s->tensor = 1;
     s->ring_first_item[nr] = (int)items.size();
     s->ring_first_sym[nr] = (int)items_sym.size();
     s->ring_first_belt[nr] = (int)items_belt.size();
@@ -201,6 +210,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         return cuda_fail(e, "upload work list");
     if ((e = dev_upload(&s->d_items_belt, items_belt.data(), items_belt.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
+    if ((e = dev_upload(&s->d_items_mma, items_mma.data(), items_mma.size())) != cudaSuccess)
+        return cuda_fail(e, "upload work list");
     if ((e = cudaMalloc(&s->d_err, sizeof(int))) != cudaSuccess)
         return cuda_fail(e, "error flag");
     if ((e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess)
@@ -272,6 +283,7 @@ ksc_split_opts resolve_opts(const ksc_split_opts *opts) {
         if (!(o.svd_rcond > 0.0)) o.svd_rcond = 1e-6;
         if (!(o.alpha > 0.0)) o.alpha = 5.0;
         if (o.path != 1) o.path = 0;
+        if (o.tensor != 1) o.tensor = 0;
     }
     return o;
 }
@@ -299,10 +311,17 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
         if (e != cudaSuccess) return cuda_fail(e, "gather kernel launch");
         return KSC_OK;
     }
-    const int a = s->ring_first_belt[r0], b = s->ring_first_belt[r1 + 1];
-    e = ksc::launch_conv_belt(s->plan, s->d_items_belt + a, b - a, s->seg_cap, d_in, d_out,
-                              n_maps, stride, s->d_err, st);
-    if (e != cudaSuccess) return cuda_fail(e, "belt kernel launch");
+    const bool whole = r0 == 0 && r1 == s->plan.nrings - 1;
+    if (whole && n_maps >= 16 && s->tensor == 0 && s->n_items_mma > 0) {
+        e = ksc::launch_conv_belt_mma(s->plan, s->d_items_mma, s->n_items_mma, s->w_cap, d_in,
+                                      d_out, n_maps, stride, s->d_err, st);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor belt kernel launch");
+    } else {
+        const int a = s->ring_first_belt[r0], b = s->ring_first_belt[r1 + 1];
+        e = ksc::launch_conv_belt(s->plan, s->d_items_belt + a, b - a, s->seg_cap, d_in, d_out,
+                                  n_maps, stride, s->d_err, st);
+        if (e != cudaSuccess) return cuda_fail(e, "belt kernel launch");
+    }
     // northern rings r whose own or mirror ring (nr - 1 - r) lies in the band
     const int nr = s->plan.nrings, eq = (nr - 1) / 2;
     int lo = nr, hi = -1;
@@ -334,6 +353,7 @@ int ksc_default_opts(ksc_split_opts *opts) {
     opts->alpha = 5.0;
     opts->n_intervals = 0;
     opts->path = 0;
+    opts->tensor = 0;
     return KSC_OK;
 }
 
@@ -538,6 +558,37 @@ int ksc_count_pairs(ksc_split *s, long long *n_pairs) {
     s->n_pairs = (long long)h[0];
     s->n_pairs_belt = (long long)h[1];
     *n_pairs = s->n_pairs;
+    return KSC_OK;
+}
+
+int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in, float *d_out,
+                                 int n_maps, int stage, void *stream) {
+    int rc = check_maps(s, d_in, d_out);
+    if (rc) return rc;
+    if (n_maps < 1 || n_maps > 65535) return fail(KSC_ERR_ARG, "n_maps outside 1..65535");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long stride = s->plan.npix;
+    cudaError_t e;
+    if (stage == 1) {
+        if (s->path == 1) return KSC_OK;
+        if (n_maps >= 16 && s->tensor == 0 && s->n_items_mma > 0)
+            e = ksc::launch_conv_belt_mma(s->plan, s->d_items_mma, s->n_items_mma, s->w_cap,
+                                          d_in, d_out, n_maps, stride, s->d_err, st);
+        else
+            e = ksc::launch_conv_belt(s->plan, s->d_items_belt, s->n_items_belt, s->seg_cap,
+                                      d_in, d_out, n_maps, stride, s->d_err, st);
+    } else if (stage == 2) {
+        if (s->path == 1)
+            e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, n_maps,
+                                         stride, 0, nullptr, st);
+        else
+            e = ksc::launch_conv_sym(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out,
+                                     n_maps, stride, s->n_items_belt > 0 ? 1 : 0, 0,
+                                     s->plan.nrings - 1, st);
+    } else {
+        return fail(KSC_ERR_ARG, "stage must be 1 or 2");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "stage launch");
     return KSC_OK;
 }
 

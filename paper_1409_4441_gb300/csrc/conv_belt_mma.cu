@@ -1,0 +1,340 @@
+// Multi-map real-space convolution of belt ring pairs on the tcgen05 tensor
+// cores (5th-generation MMA, accumulators in tensor memory).
+//
+// For n maps sharing one kernel, the contribution of belt input ring r' to a
+// block of 128 consecutive outputs of belt ring r is a dense contraction
+//
+//   D[k][n] += sum_j W[k][j] X[n][j],   W[k][j] = w_{r r'}[Delta_0 + j - k]
+//
+// with X[n][j] = m_n(r', k0 + Delta_0 + j): the circulant kernel block (a
+// Toeplitz band of the ring pair's weight vector, zero outside it) times the
+// stack of maps.  M = 128 outputs (TMEM lanes), N = 64 maps (TMEM columns),
+// K = 128 + window in tiles of 32.  FP32 accuracy from TF32 tensor cores:
+// every operand is split into a TF32 high part and a TF32 residual and three
+// MMAs (hi*hi + hi*lo + lo*hi) accumulate in FP32.
+//
+// Each CTA (4 warps) owns one 128-output block and one group of 64 maps and
+// walks the belt input rings.  Per ring pair all threads compute the weight
+// vector, then build the operand tiles (the Toeplitz band and the maps, split,
+// in the no-swizzle K-major canonical layout) into one of two shared-memory
+// stages while one thread issues the MMAs of the other stage and commits them
+// to that stage's mbarrier.  After the last tile of a ring pair the partial
+// accumulator is read back from TMEM (tcgen05.ld) and Kahan-folded into FP32
+// totals in shared memory, so that FP32 rounding stays per ring pair.  Every
+// mbarrier wait is bounded; on a timeout the kernel raises the device error
+// flag, drains its commits and frees its tensor memory before returning.
+#include <cstdint>
+
+#include "ksc_device.cuh"
+#include "ksc_internal.h"
+
+namespace ksc {
+namespace {
+
+constexpr int kM = 128;            // outputs per block (TMEM lanes)
+constexpr int kN = 64;             // maps per group (TMEM columns)
+constexpr int kKT = 32;            // K per shared-memory tile (4 MMAs of K = 8)
+constexpr int kThreads = 128;
+constexpr int kMaxWait = 1 << 22;
+constexpr int kTotStride = kN + 1;  // padded rows: conflict-free per-row access
+
+struct Stage {  // one operand stage, canonical no-swizzle K-major tiles
+    float a_hi[kM * kKT];
+    float a_lo[kM * kKT];
+    float b_hi[kN * kKT];
+    float b_lo[kN * kKT];
+};
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// element (row, k) of a K-major tile with kKT columns: 8-row x 16-byte core
+// matrices, K-adjacent core matrices 128 B apart, 8-row groups kKT*32 B apart
+__device__ __forceinline__ int toff(int row, int k) {
+    return (row >> 3) * (kKT * 8) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr(p) & 0x3FFFF) >> 4);
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;        // leading (K) core-matrix stride
+    d |= (uint64_t)(((kKT * 32u) >> 4) & 0x3FFF) << 32;  // stride (8-row group) offset
+    d |= (uint64_t)1 << 46;                              // descriptor version
+    return d;                                            // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ void split_tf32(float x, float *hi, float *lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float hf = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hf));
+    *hi = hf;
+    *lo = __uint_as_float(l);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < kMaxWait; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(saddr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            saddr(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
+                     const float *__restrict__ in, float *__restrict__ out, int n_maps,
+                     long long map_stride, int w_cap, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Stage *stage = reinterpret_cast<Stage *>(smem_raw);            // 2 stages
+    float *tot = reinterpret_cast<float *>(stage + 2);             // kM x kTotStride
+    float *cmp = tot + kM * kTotStride;                            // Kahan compensation
+    float *wbuf = cmp + kM * kTotStride;                           // w_cap weights
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g0 = blockIdx.y * kN;  // first map of this CTA's group
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(&tmem_base)),
+                     "r"(kN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                           ((uint32_t)(kM >> 4) << 24);  // F32 += TF32 x TF32, K-major
+    uint32_t phase[2] = {0u, 0u};
+    int pending[2] = {0, 0};
+    bool ok = true;
+
+    for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        const int r = items[it].x, k0 = items[it].y;
+        const DevRing R = P.d_rings[r];
+        const int L = R.len;
+        const int2 rg = P.d_range[r];
+        const int q_lo = max(rg.x, P.belt_lo), q_hi = min(rg.y, P.belt_hi);
+        const PairInfo *pinfo = P.d_pairs + P.d_pair_base[r] - rg.x;
+        for (int n = 0; n < kN; ++n) {
+            tot[tid * kTotStride + n] = 0.0f;
+            cmp[tid * kTotStride + n] = 0.0f;
+        }
+        int tcount = 0;  // tiles issued for this item
+        for (int q = q_lo; q <= q_hi && ok; ++q) {
+            const PairInfo pi = pinfo[q];
+            if (pi.w < 0) continue;
+            const DevRing Qr = P.d_rings[q];
+            // window of Delta (as in the FFMA belt kernel)
+            int lo = -pi.w, hi = pi.w;
+            if (hi - lo + 1 >= L) {
+                lo = -(L / 2);
+                hi = lo + L - 1;
+            }
+            const int nd = hi - lo + 1;
+            if (nd > w_cap) {  // never expected: the host sized w_cap for every pair
+                if (tid == 0) atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
+                continue;
+            }
+            __syncthreads();  // previous wbuf readers are done
+            const DF A = DF{pi.Ah, pi.Al}, B = DF{pi.Bh, pi.Bl}, c1 = DF{P.belt_c1h, P.belt_c1l};
+            const int tdiff = R.phase - Qr.phase;
+            for (int j = tid; j < nd; j += kThreads) {
+                const int D = lo + j;
+                const float mf = (float)(tdiff - 2 * D);
+                const float xh = mf * c1.h;
+                const float xl = fmaf(mf, c1.h, -xh) + mf * c1.l;
+                int ti;
+                float f;
+                float wv = 0.0f;
+                if (chord_to_table_padded(A, B, sin_df(xh, xl), P.nint2, &ti, &f))
+                    wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
+                wbuf[j] = wv;
+            }
+            __syncthreads();
+            const int ktot = kM + nd - 1;
+            const int nkt = (ktot + kKT - 1) / kKT;
+            const float *mq = in + (long long)Qr.start;
+            for (int t = 0; t < nkt; ++t) {
+                const int b = tcount & 1;
+                if (pending[b]) {  // the MMAs that last read this stage must be done
+                    if (!mbar_wait(&bar[b], phase[b])) s_abort = 1;
+                    phase[b] ^= 1u;
+                    pending[b] = 0;
+                }
+                Stage &S = stage[b];
+                // Toeplitz band: A[m][jj] = w[32t + jj - m]
+                for (int e = tid; e < kM * kKT; e += kThreads) {
+                    const int m = e >> 5, jj = e & 31;
+                    const int idx = kKT * t + jj - m;
+                    const float v = (idx >= 0 && idx < nd) ? wbuf[idx] : 0.0f;
+                    float h, l;
+                    split_tf32(v, &h, &l);
+                    S.a_hi[toff(m, jj)] = h;
+                    S.a_lo[toff(m, jj)] = l;
+                }
+                // maps: X[n][jj] = m_n(r', k0 + lo + 32t + jj)
+                for (int e = tid; e < kN * kKT; e += kThreads) {
+                    const int n = e >> 5, jj = e & 31;
+                    const int j = kKT * t + jj;
+                    float v = 0.0f;
+                    if (j < ktot && g0 + n < n_maps) {
+                        int p = (k0 + lo + j) % L;
+                        if (p < 0) p += L;
+                        v = __ldg(mq + (long long)(g0 + n) * map_stride + p);
+                    }
+                    float h, l;
+                    split_tf32(v, &h, &l);
+                    S.b_hi[toff(n, jj)] = h;
+                    S.b_lo[toff(n, jj)] = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (s_abort) {  // uniform: read after the barrier
+                    ok = false;
+                    break;
+                }
+                if (tid == 0) {
+#pragma unroll
+                    for (int s = 0; s < kKT / 8; ++s) {
+                        const uint64_t ah = smem_desc(S.a_hi + s * 64), al = smem_desc(S.a_lo + s * 64);
+                        const uint64_t bh = smem_desc(S.b_hi + s * 64), bl = smem_desc(S.b_lo + s * 64);
+                        const uint32_t first = (t == 0 && s == 0) ? 0u : 1u;  // new partial per pair
+                        mma_tf32(tmem, ah, bh, idesc, first);
+                        mma_tf32(tmem, ah, bl, idesc, 1u);
+                        mma_tf32(tmem, al, bh, idesc, 1u);
+                    }
+                    mma_commit(&bar[b]);
+                }
+                pending[b] = 1;
+                ++tcount;
+            }
+            if (!ok) break;
+            // drain: every MMA of this ring pair has completed
+            for (int bb = 0; bb < 2; ++bb) {
+                const int b = (tcount + bb) & 1;  // older stage first
+                if (pending[b]) {
+                    if (!mbar_wait(&bar[b], phase[b])) s_abort = 1;
+                    phase[b] ^= 1u;
+                    pending[b] = 0;
+                }
+            }
+            __syncthreads();
+            if (s_abort) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // fold this ring pair's partial (row tid = warp*32 + lane) into the totals
+#pragma unroll
+            for (int c0 = 0; c0 < kN; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                    "%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int jv = 0; jv < 16; ++jv) {
+                    float *s = tot + tid * kTotStride + c0 + jv;
+                    float *cc = cmp + tid * kTotStride + c0 + jv;
+                    const float y = __uint_as_float(v[jv]) - *cc;
+                    const float tt = *s + y;
+                    *cc = (tt - *s) - y;
+                    *s = tt;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        if (!ok) break;
+        // write this block: output row tid, maps g0 .. g0 + kN - 1
+        const int k = k0 + tid;
+        if (k < L) {
+            for (int n = 0; n < kN && g0 + n < n_maps; ++n)
+                out[(long long)(g0 + n) * map_stride + R.start + k] =
+                    tot[tid * kTotStride + n] * P.domega;
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
+        for (int b = 0; b < 2; ++b)  // bounded drain of commits still in flight
+            if (pending[b]) mbar_wait(&bar[b], phase[b]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN));
+}
+
+} // namespace
+
+int belt_mma_block() { return kM; }
+int belt_mma_maps() { return kN; }
+
+size_t belt_mma_smem(int w_cap) {
+    return 2 * sizeof(Stage) + sizeof(float) * (2 * kM * kTotStride + (size_t)w_cap);
+}
+
+cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_items, int w_cap,
+                                 const float *d_in, float *d_out, int n_maps,
+                                 long long map_stride, int *d_err, cudaStream_t st) {
+    if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    const size_t smem = belt_mma_smem(w_cap);
+    cudaError_t e = cudaFuncSetAttribute(conv_belt_mma_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int groups = (n_maps + kN - 1) / kN;
+    int blocks = n_sm;  // one CTA per SM (shared memory and 64 TMEM columns each)
+    if (blocks > n_items) blocks = n_items;
+    dim3 grid(blocks, groups);
+    conv_belt_mma_kernel<<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out, n_maps,
+                                                       map_stride, w_cap, d_err);
+    return cudaGetLastError();
+}
+
+} // namespace ksc

@@ -112,6 +112,15 @@ cudaError_t launch_conv_belt(const ConvPlan &p, const int2 *d_items, int n_items
                              int seg_cap, const float *d_in, float *d_out, int n_maps,
                              long long map_stride, int *d_err, cudaStream_t st);
 
+// tcgen05 multi-map kernel for belt ring pairs: items are (belt ring, first
+// pixel) blocks of belt_mma_block() outputs; maps in groups of belt_mma_maps().
+int belt_mma_block();
+int belt_mma_maps();
+size_t belt_mma_smem(int w_cap);
+cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_items, int w_cap,
+                                 const float *d_in, float *d_out, int n_maps,
+                                 long long map_stride, int *d_err, cudaStream_t st);
+
 // Symmetric gather over northern rings (and the equator): each thread owns
 // one first-quarter position and writes its eight images; only output rings
 // in [band_lo, band_hi] are written.  Items are (ring, first quarter position)
@@ -158,6 +167,10 @@ struct ksc_split {
     int n_items_belt = 0;
     std::vector<int> ring_first_belt;
     int seg_cap = 0;
+    int2 *d_items_mma = nullptr;           // 128-output belt blocks for the tensor kernel
+    int n_items_mma = 0;
+    int w_cap = 0;                         // widest belt weight window
+    int tensor = 0;                        // 0: tensor kernel for >= 16 maps, 1: never
     int *d_err = nullptr;                  // device error flag (bounded waits)
     ksc::ConvPlan plan{};
 

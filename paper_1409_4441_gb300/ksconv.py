@@ -36,7 +36,8 @@ EXPORTS = [
     "ksc_default_opts", "ksc_make_split", "ksc_make_split_real", "ksc_split_info",
     "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
     "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
-    "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_count_pairs", "ksc_device_status",
+    "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_conv_real_multimap_stage",
+    "ksc_count_pairs", "ksc_device_status",
     "ksc_free_split", "ksc_build_table_noalloc",
     "ksc_status_string", "ksc_last_error",
 ]
@@ -45,7 +46,8 @@ EXPORTS = [
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("oversample", ctypes.c_int),
                 ("svd_rcond", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("n_intervals", ctypes.c_int), ("path", ctypes.c_int)]
+                ("n_intervals", ctypes.c_int), ("path", ctypes.c_int),
+                ("tensor", ctypes.c_int)]
 
 
 class Desc(ctypes.Structure):
@@ -74,6 +76,7 @@ _sig = {
     "ksc_conv_real_batch": [_vp, _vp, _vp, _i, _vp],
     "ksc_conv_real_host": [_vp, _vp, _vp],
     "ksc_conv_real_stage": [_vp, _vp, _vp, _i, _vp],
+    "ksc_conv_real_multimap_stage": [_vp, _vp, _vp, _i, _i, _vp],
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
@@ -235,6 +238,12 @@ def conv_real(s: Split, d_in, d_out, stream=None):
 def conv_real_stage(s: Split, d_in, d_out, stage: int, stream=None):
     _check(_lib.ksc_conv_real_stage(s.handle, _dptr(d_in), _dptr(d_out), stage, _stream(stream)),
            "ksc_conv_real_stage")
+    return d_out
+
+
+def conv_real_multimap_stage(s: Split, d_in, d_out, n_maps: int, stage: int, stream=None):
+    _check(_lib.ksc_conv_real_multimap_stage(s.handle, _dptr(d_in), _dptr(d_out), n_maps, stage,
+                                             _stream(stream)), "ksc_conv_real_multimap_stage")
     return d_out
 
 

@@ -37,8 +37,8 @@ def test_status_strings_and_defaults(K):
     assert K._lib.ksc_status_string(K.KSC_ERR_ARG) == b"KSC_ERR_ARG"
     assert K._lib.ksc_status_string(-99) == b"KSC_ERR_UNKNOWN"
     o = K.default_opts()
-    assert (o.mode, o.oversample, o.svd_rcond, o.alpha, o.n_intervals, o.path) == \
-        (0, 2, 1e-6, 5.0, 0, 0)
+    assert (o.mode, o.oversample, o.svd_rcond, o.alpha, o.n_intervals, o.path, o.tensor) == \
+        (0, 2, 1e-6, 5.0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("nside,lcut,tc,lmax", [
