@@ -155,7 +155,11 @@ int ksc_conv_real_rings(const ksc_split *s, const float *d_in, float *d_out,
 
 /*
  * n_maps maps sharing one split: d_in and d_out are [n_maps][12 nside^2]
- * device arrays (map-major).  Asynchronous.
+ * device arrays (map-major).  Asynchronous.  With n_maps >= 16 the belt ring
+ * pairs run on the tensor cores through a per-split workspace (the map stack
+ * pre-split into TF32 tiles, about 2.6x the input size), allocated on the
+ * first such call and reused; multi-map calls on one split must therefore not
+ * overlap on the GPU.
  */
 int ksc_conv_real_multimap(const ksc_split *s, const float *d_in,
                            float *d_out, int n_maps, void *stream);

@@ -47,6 +47,7 @@ void release(ksc_split *s) {
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
     cudaFree(s->d_items_mma);
+    cudaFree(s->d_ws);
     cudaFree(s->d_items_belt);
     cudaFree(s->d_err);
     cudaFree(s->d_io);
@@ -104,7 +105,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     s->ring_first_sym.assign(nr + 1, 0);
     s->ring_first_belt.assign(nr + 1, 0);
     const int bc = ksc::belt_chunk();
-    int max_nd = 0;
+    int max_nd = 0, w_ext = 0;
     for (int r = 0; r < nr; ++r) {
         s->ring_first_item[r] = (int)items.size();
         s->ring_first_sym[r] = (int)items_sym.size();
@@ -126,6 +127,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                 int w = (int)std::ceil(dphi * L / (2.0 * kPi)) + 1;  // same as PairInfo::w
                 int n = std::min(2 * w + 1, L);
                 max_nd = std::max(max_nd, n);
+                w_ext = std::max(w_ext, 2 * w + 1 >= L ? L / 2 : w);
             }
         }
     }
@@ -136,6 +138,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     s->n_items_mma = (int)items_mma.size();
     s->w_cap = (max_nd + 2 * 13 + 3) & ~3;
     s->tensor = o.tensor;
+    s->mma_ext0 = ((w_ext + 32) + 31) & ~31;
+    s->mma_ntiles = (s->mma_ext0 + 4 * nside + (((w_ext + 160) + 31) & ~31)) / 32;
     if (ksc::belt_mma_smem(s->w_cap) > 220u * 1024) s->tensor = 1;
     s->ring_first_item[nr] = (int)items.size();
     s->ring_first_sym[nr] = (int)items_sym.size();
@@ -297,6 +301,28 @@ int check_maps(const ksc_split *s, const void *a, const void *b) {
     return KSC_OK;
 }
 
+// Tensor-core belt stage for a stack of maps; grows the split's pre-tiled map
+// workspace on first use (calls on one split must not overlap on the GPU).
+int launch_belt_tensor(const ksc_split *cs, const float *d_in, float *d_out, int n_maps,
+                       long long stride, cudaStream_t st) {
+    ksc_split *s = const_cast<ksc_split *>(cs);
+    const int n_belt = s->plan.belt_hi - s->plan.belt_lo + 1;
+    const size_t need = ksc::belt_mma_workspace_floats(n_belt, s->mma_ntiles, n_maps);
+    if (s->ws_floats < need) {
+        cudaFree(s->d_ws);
+        s->d_ws = nullptr;
+        s->ws_floats = 0;
+        if (cudaMalloc(&s->d_ws, need * sizeof(float)) != cudaSuccess)
+            return fail(KSC_ERR_NOMEM, "tensor-path workspace");
+        s->ws_floats = need;
+    }
+    cudaError_t e = ksc::launch_conv_belt_mma(s->plan, s->d_items_mma, s->n_items_mma, s->w_cap,
+                                              s->mma_ntiles, s->mma_ext0, s->d_ws, d_in, d_out,
+                                              n_maps, stride, s->d_err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor belt kernel launch");
+    return KSC_OK;
+}
+
 // The real-space convolution of output rings [r0, r1] (0-based, inclusive).
 // Default path: circulant belt kernel first (writes belt outputs), then the
 // symmetric gather (writes cap outputs, adds cap inputs to belt outputs).
@@ -313,9 +339,8 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
     }
     const bool whole = r0 == 0 && r1 == s->plan.nrings - 1;
     if (whole && n_maps >= 16 && s->tensor == 0 && s->n_items_mma > 0) {
-        e = ksc::launch_conv_belt_mma(s->plan, s->d_items_mma, s->n_items_mma, s->w_cap, d_in,
-                                      d_out, n_maps, stride, s->d_err, st);
-        if (e != cudaSuccess) return cuda_fail(e, "tensor belt kernel launch");
+        int rc = launch_belt_tensor(s, d_in, d_out, n_maps, stride, st);
+        if (rc) return rc;
     } else {
         const int a = s->ring_first_belt[r0], b = s->ring_first_belt[r1 + 1];
         e = ksc::launch_conv_belt(s->plan, s->d_items_belt + a, b - a, s->seg_cap, d_in, d_out,
@@ -572,8 +597,7 @@ int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in, float *d
     if (stage == 1) {
         if (s->path == 1) return KSC_OK;
         if (n_maps >= 16 && s->tensor == 0 && s->n_items_mma > 0)
-            e = ksc::launch_conv_belt_mma(s->plan, s->d_items_mma, s->n_items_mma, s->w_cap,
-                                          d_in, d_out, n_maps, stride, s->d_err, st);
+            return launch_belt_tensor(s, d_in, d_out, n_maps, stride, st);
         else
             e = ksc::launch_conv_belt(s->plan, s->d_items_belt, s->n_items_belt, s->seg_cap,
                                       d_in, d_out, n_maps, stride, s->d_err, st);

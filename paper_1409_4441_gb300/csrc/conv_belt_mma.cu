@@ -4,25 +4,26 @@
 // For n maps sharing one kernel, the contribution of belt input ring r' to a
 // block of 128 consecutive outputs of belt ring r is a dense contraction
 //
-//   D[k][n] += sum_j W[k][j] X[n][j],   W[k][j] = w_{r r'}[Delta_0 + j - k]
+//   D[k][n] += sum_j W[k][j] X[n][j],   W[k][j] = w_{r r'}[p_j - k]
 //
-// with X[n][j] = m_n(r', k0 + Delta_0 + j): the circulant kernel block (a
-// Toeplitz band of the ring pair's weight vector, zero outside it) times the
-// stack of maps.  M = 128 outputs (TMEM lanes), N = 64 maps (TMEM columns),
-// K = 128 + window in tiles of 32.  FP32 accuracy from TF32 tensor cores:
-// every operand is split into a TF32 high part and a TF32 residual and three
-// MMAs (hi*hi + hi*lo + lo*hi) accumulate in FP32.
+// over input positions p_j of ring r': the circulant kernel block (a Toeplitz
+// band of the ring pair's weight vector, zero outside it) times the stack of
+// maps.  M = 128 outputs (TMEM lanes), N = 64 maps (TMEM columns), K in tiles
+// of 32 positions aligned to absolute ring positions.  FP32 accuracy from TF32
+// tensor cores: operands are split into a TF32 high part and a TF32 residual
+// and three MMAs (hi*hi + hi*lo + lo*hi) accumulate in FP32.
 //
-// Each CTA (4 warps) owns one 128-output block and one group of 64 maps and
-// walks the belt input rings.  Per ring pair all threads compute the weight
-// vector, then build the operand tiles (the Toeplitz band and the maps, split,
-// in the no-swizzle K-major canonical layout) into one of two shared-memory
-// stages while one thread issues the MMAs of the other stage and commits them
-// to that stage's mbarrier.  After the last tile of a ring pair the partial
-// accumulator is read back from TMEM (tcgen05.ld) and Kahan-folded into FP32
-// totals in shared memory, so that FP32 rounding stays per ring pair.  Every
+// belt_tile_prep_kernel writes, once per call, every belt ring of every map
+// group as pre-split K x N tiles already in the canonical no-swizzle K-major
+// layout (ring positions extended past both ends, so windows never wrap).  The
+// contraction kernel then fetches each B tile with one 1-D TMA bulk copy
+// (cp.async.bulk + mbarrier) issued before the threads build the matching A
+// tile (weights split once per ring pair, 16-byte stores), so copy, build and
+// the MMAs of the previous stage overlap.  After the last tile of a ring pair
+// the partial accumulator is read back (tcgen05.ld) and Kahan-folded into FP32
+// totals in shared memory, so FP32 rounding stays per ring pair.  Every
 // mbarrier wait is bounded; on a timeout the kernel raises the device error
-// flag, drains its commits and frees its tensor memory before returning.
+// flag, drains its pending operations and frees its tensor memory.
 #include <cstdint>
 
 #include "ksc_device.cuh"
@@ -31,18 +32,18 @@
 namespace ksc {
 namespace {
 
-constexpr int kM = 128;            // outputs per block (TMEM lanes)
-constexpr int kN = 64;             // maps per group (TMEM columns)
-constexpr int kKT = 32;            // K per shared-memory tile (4 MMAs of K = 8)
+constexpr int kM = 128;             // outputs per block (TMEM lanes)
+constexpr int kN = 64;              // maps per group (TMEM columns)
+constexpr int kKT = 32;             // positions per K tile (4 MMAs of K = 8)
 constexpr int kThreads = 128;
 constexpr int kMaxWait = 1 << 22;
 constexpr int kTotStride = kN + 1;  // padded rows: conflict-free per-row access
+constexpr int kTileB = kN * kKT;    // floats per B tile part (hi or lo)
 
 struct Stage {  // one operand stage, canonical no-swizzle K-major tiles
     float a_hi[kM * kKT];
     float a_lo[kM * kKT];
-    float b_hi[kN * kKT];
-    float b_lo[kN * kKT];
+    float b[2 * kTileB];  // hi then lo, copied as one block
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) {
@@ -51,7 +52,7 @@ __device__ __forceinline__ uint32_t saddr(const void *p) {
 
 // element (row, k) of a K-major tile with kKT columns: 8-row x 16-byte core
 // matrices, K-adjacent core matrices 128 B apart, 8-row groups kKT*32 B apart
-__device__ __forceinline__ int toff(int row, int k) {
+__host__ __device__ __forceinline__ int toff(int row, int k) {
     return (row >> 3) * (kKT * 8) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
 }
 
@@ -103,21 +104,61 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
         : "memory");
 }
 
+// B tiles: for belt ring index qi, tile u (positions 32u - ext0 .. +31),
+// map group g: kN x kKT hi floats then kN x kKT lo floats.
+__global__ void belt_tile_prep_kernel(const ConvPlan P, const float *__restrict__ in,
+                                      int n_maps, long long map_stride, int n_tiles, int ext0,
+                                      int n_groups, float *__restrict__ ws) {
+    const long long quads = (long long)(P.belt_hi - P.belt_lo + 1) * n_tiles * n_groups * kN *
+                            (kKT / 4);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < quads;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int kq = (int)(e % (kKT / 4));
+        long long rest = e / (kKT / 4);
+        const int n = (int)(rest % kN);
+        rest /= kN;
+        const int g = (int)(rest % n_groups);
+        rest /= n_groups;
+        const int u = (int)(rest % n_tiles);
+        const int qi = (int)(rest / n_tiles);
+        const DevRing Q = P.d_rings[P.belt_lo + qi];
+        const int L = Q.len;
+        const int map = g * kN + n;
+        float hi[4], lo[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v = 0.0f;
+            if (map < n_maps) {
+                int p = (u * kKT + kq * 4 + c - ext0) % L;
+                if (p < 0) p += L;
+                v = __ldg(in + (long long)map * map_stride + Q.start + p);
+            }
+            split_tf32(v, &hi[c], &lo[c]);
+        }
+        float *blk = ws + (((long long)qi * n_tiles + u) * n_groups + g) * (2 * kTileB);
+        const int o = toff(n, kq * 4);
+        *reinterpret_cast<float4 *>(blk + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4 *>(blk + kTileB + o) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
-                     const float *__restrict__ in, float *__restrict__ out, int n_maps,
-                     long long map_stride, int w_cap, int *__restrict__ err) {
+                     const float *__restrict__ ws, int n_tiles, int ext0, int n_groups,
+                     float *__restrict__ out, int n_maps, long long map_stride, int w_cap,
+                     int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Stage *stage = reinterpret_cast<Stage *>(smem_raw);            // 2 stages
-    float *tot = reinterpret_cast<float *>(stage + 2);             // kM x kTotStride
-    float *cmp = tot + kM * kTotStride;                            // Kahan compensation
-    float *wbuf = cmp + kM * kTotStride;                           // w_cap weights
-    __shared__ __align__(8) uint64_t bar[2];
+    Stage *stage = reinterpret_cast<Stage *>(smem_raw);  // 2 stages
+    float *tot = reinterpret_cast<float *>(stage + 2);   // kM x kTotStride
+    float *cmp = tot + kM * kTotStride;                  // Kahan compensation
+    float *whi = cmp + kM * kTotStride;                  // w_cap split weights
+    float *wlo = whi + w_cap;
+    __shared__ __align__(8) uint64_t bfull[2], mdone[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int g0 = blockIdx.y * kN;  // first map of this CTA's group
+    const int g = blockIdx.y;  // map group
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          saddr(&tmem_base)),
@@ -125,8 +166,10 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bar[1])));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&bfull[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mdone[b])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -136,8 +179,9 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
                            ((uint32_t)(kM >> 4) << 24);  // F32 += TF32 x TF32, K-major
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t ph_full[2] = {0u, 0u}, ph_done[2] = {0u, 0u};
     int pending[2] = {0, 0};
+    int copy_b = -1;  // stage of the last bulk copy thread 0 issued and has not waited for
     bool ok = true;
 
     for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
@@ -151,12 +195,11 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
             tot[tid * kTotStride + n] = 0.0f;
             cmp[tid * kTotStride + n] = 0.0f;
         }
-        int tcount = 0;  // tiles issued for this item
+        int tcount = 0;
         for (int q = q_lo; q <= q_hi && ok; ++q) {
             const PairInfo pi = pinfo[q];
             if (pi.w < 0) continue;
             const DevRing Qr = P.d_rings[q];
-            // window of Delta (as in the FFMA belt kernel)
             int lo = -pi.w, hi = pi.w;
             if (hi - lo + 1 >= L) {
                 lo = -(L / 2);
@@ -167,57 +210,72 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
                 if (tid == 0) atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
                 continue;
             }
-            __syncthreads();  // previous wbuf readers are done
-            const DF A = DF{pi.Ah, pi.Al}, B = DF{pi.Bh, pi.Bl}, c1 = DF{P.belt_c1h, P.belt_c1l};
-            const int tdiff = R.phase - Qr.phase;
-            for (int j = tid; j < nd; j += kThreads) {
-                const int D = lo + j;
-                const float mf = (float)(tdiff - 2 * D);
-                const float xh = mf * c1.h;
-                const float xl = fmaf(mf, c1.h, -xh) + mf * c1.l;
-                int ti;
-                float f;
-                float wv = 0.0f;
-                if (chord_to_table_padded(A, B, sin_df(xh, xl), P.nint2, &ti, &f))
-                    wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
-                wbuf[j] = wv;
+            __syncthreads();  // previous readers of whi / wlo are done
+            {
+                const DF A = DF{pi.Ah, pi.Al}, B = DF{pi.Bh, pi.Bl};
+                const DF c1 = DF{P.belt_c1h, P.belt_c1l};
+                const int tdiff = R.phase - Qr.phase;
+                for (int j = tid; j < nd; j += kThreads) {
+                    const int D = lo + j;
+                    const float mf = (float)(tdiff - 2 * D);
+                    const float xh = mf * c1.h;
+                    const float xl = fmaf(mf, c1.h, -xh) + mf * c1.l;
+                    int ti;
+                    float f;
+                    float wv = 0.0f;
+                    if (chord_to_table_padded(A, B, sin_df(xh, xl), P.nint2, &ti, &f))
+                        wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
+                    split_tf32(wv, &whi[j], &wlo[j]);
+                }
             }
             __syncthreads();
-            const int ktot = kM + nd - 1;
-            const int nkt = (ktot + kKT - 1) / kKT;
-            const float *mq = in + (long long)Qr.start;
-            for (int t = 0; t < nkt; ++t) {
+            // K tiles aligned to absolute positions: p in [P0, P1]
+            const int P0 = (k0 + lo) & ~(kKT - 1);
+            const int P1 = k0 + kM - 1 + hi;
+            const int u0 = (P0 + ext0) / kKT, u1 = (P1 + ext0) / kKT;
+            const float *blk0 = ws + (((long long)(q - P.belt_lo) * n_tiles) * n_groups + g) *
+                                         (2 * kTileB);
+            const long long ustride = (long long)n_groups * (2 * kTileB);
+            const int base = P0 - k0 - lo;  // weight index of (row 0, column 0)
+            for (int u = u0; u <= u1; ++u) {
                 const int b = tcount & 1;
-                if (pending[b]) {  // the MMAs that last read this stage must be done
-                    if (!mbar_wait(&bar[b], phase[b])) s_abort = 1;
-                    phase[b] ^= 1u;
+                if (pending[b]) {  // the MMAs that last read this stage are done
+                    if (!mbar_wait(&mdone[b], ph_done[b])) s_abort = 1;
+                    ph_done[b] ^= 1u;
                     pending[b] = 0;
                 }
                 Stage &S = stage[b];
-                // Toeplitz band: A[m][jj] = w[32t + jj - m]
-                for (int e = tid; e < kM * kKT; e += kThreads) {
-                    const int m = e >> 5, jj = e & 31;
-                    const int idx = kKT * t + jj - m;
-                    const float v = (idx >= 0 && idx < nd) ? wbuf[idx] : 0.0f;
-                    float h, l;
-                    split_tf32(v, &h, &l);
-                    S.a_hi[toff(m, jj)] = h;
-                    S.a_lo[toff(m, jj)] = l;
+                if (tid == 0 && !s_abort) {  // B tile: one bulk copy
+                    const uint32_t bytes = 2u * kTileB * 4u;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                     saddr(&bfull[b])),
+                                 "r"(bytes)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], "
+                        "[%1], %2, [%3];" ::"r"(saddr(S.b)),
+                        "l"(blk0 + (long long)u * ustride), "r"(bytes), "r"(saddr(&bfull[b]))
+                        : "memory");
+                    copy_b = b;
                 }
-                // maps: X[n][jj] = m_n(r', k0 + lo + 32t + jj)
-                for (int e = tid; e < kN * kKT; e += kThreads) {
-                    const int n = e >> 5, jj = e & 31;
-                    const int j = kKT * t + jj;
-                    float v = 0.0f;
-                    if (j < ktot && g0 + n < n_maps) {
-                        int p = (k0 + lo + j) % L;
-                        if (p < 0) p += L;
-                        v = __ldg(mq + (long long)(g0 + n) * map_stride + p);
+                // A tile row tid: A[m][jj] = w[base + 32 (u - u0) + jj - m]
+                {
+                    const int m = tid;
+                    const int wi0 = base + kKT * (u - u0) - m;
+#pragma unroll
+                    for (int jq = 0; jq < kKT; jq += 4) {
+                        float h[4], l[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int wi = wi0 + jq + c;
+                            const bool in = wi >= 0 && wi < nd;
+                            h[c] = in ? whi[wi] : 0.0f;
+                            l[c] = in ? wlo[wi] : 0.0f;
+                        }
+                        const int o = toff(m, jq);
+                        *reinterpret_cast<float4 *>(S.a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<float4 *>(S.a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
                     }
-                    float h, l;
-                    split_tf32(v, &h, &l);
-                    S.b_hi[toff(n, jj)] = h;
-                    S.b_lo[toff(n, jj)] = l;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -228,17 +286,25 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
                     break;
                 }
                 if (tid == 0) {
+                    copy_b = -1;
+                    if (!mbar_wait(&bfull[b], ph_full[b])) {
+                        s_abort = 1;
+                    } else {
 #pragma unroll
-                    for (int s = 0; s < kKT / 8; ++s) {
-                        const uint64_t ah = smem_desc(S.a_hi + s * 64), al = smem_desc(S.a_lo + s * 64);
-                        const uint64_t bh = smem_desc(S.b_hi + s * 64), bl = smem_desc(S.b_lo + s * 64);
-                        const uint32_t first = (t == 0 && s == 0) ? 0u : 1u;  // new partial per pair
-                        mma_tf32(tmem, ah, bh, idesc, first);
-                        mma_tf32(tmem, ah, bl, idesc, 1u);
-                        mma_tf32(tmem, al, bh, idesc, 1u);
+                        for (int s = 0; s < kKT / 8; ++s) {
+                            const uint64_t ah = smem_desc(S.a_hi + s * 64);
+                            const uint64_t al = smem_desc(S.a_lo + s * 64);
+                            const uint64_t bh = smem_desc(S.b + s * 64);
+                            const uint64_t bl = smem_desc(S.b + kTileB + s * 64);
+                            const uint32_t first = (u == u0 && s == 0) ? 0u : 1u;
+                            mma_tf32(tmem, ah, bh, idesc, first);
+                            mma_tf32(tmem, ah, bl, idesc, 1u);
+                            mma_tf32(tmem, al, bh, idesc, 1u);
+                        }
+                        mma_commit(&mdone[b]);
                     }
-                    mma_commit(&bar[b]);
                 }
+                ph_full[b] ^= 1u;
                 pending[b] = 1;
                 ++tcount;
             }
@@ -247,8 +313,8 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
             for (int bb = 0; bb < 2; ++bb) {
                 const int b = (tcount + bb) & 1;  // older stage first
                 if (pending[b]) {
-                    if (!mbar_wait(&bar[b], phase[b])) s_abort = 1;
-                    phase[b] ^= 1u;
+                    if (!mbar_wait(&mdone[b], ph_done[b])) s_abort = 1;
+                    ph_done[b] ^= 1u;
                     pending[b] = 0;
                 }
             }
@@ -258,7 +324,7 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // fold this ring pair's partial (row tid = warp*32 + lane) into the totals
+            // fold this ring pair's partial (row tid = TMEM lane) into the totals
 #pragma unroll
             for (int c0 = 0; c0 < kN; c0 += 16) {
                 uint32_t v[16];
@@ -284,19 +350,22 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         if (!ok) break;
-        // write this block: output row tid, maps g0 .. g0 + kN - 1
         const int k = k0 + tid;
         if (k < L) {
-            for (int n = 0; n < kN && g0 + n < n_maps; ++n)
-                out[(long long)(g0 + n) * map_stride + R.start + k] =
+            for (int n = 0; n < kN && g * kN + n < n_maps; ++n)
+                out[(long long)(g * kN + n) * map_stride + R.start + k] =
                     tot[tid * kTotStride + n] * P.domega;
         }
         __syncthreads();
     }
     if (!ok) {
-        if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
-        for (int b = 0; b < 2; ++b)  // bounded drain of commits still in flight
-            if (pending[b]) mbar_wait(&bar[b], phase[b]);
+        if (tid == 0) {
+            atomicExch(err, KSC_ERR_TIMEOUT);
+            if (copy_b >= 0) mbar_wait(&bfull[copy_b], ph_full[copy_b]);  // bulk copy in flight
+        }
+        for (int b = 0; b < 2; ++b) {  // bounded drain of MMAs still in flight
+            if (pending[b]) mbar_wait(&mdone[b], ph_done[b]);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -310,12 +379,18 @@ int belt_mma_block() { return kM; }
 int belt_mma_maps() { return kN; }
 
 size_t belt_mma_smem(int w_cap) {
-    return 2 * sizeof(Stage) + sizeof(float) * (2 * kM * kTotStride + (size_t)w_cap);
+    return 2 * sizeof(Stage) + sizeof(float) * (2 * kM * kTotStride + 2 * (size_t)w_cap);
+}
+
+size_t belt_mma_workspace_floats(int n_belt, int n_tiles, int n_maps) {
+    const int groups = (n_maps + kN - 1) / kN;
+    return (size_t)n_belt * n_tiles * groups * 2 * kTileB;
 }
 
 cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_items, int w_cap,
-                                 const float *d_in, float *d_out, int n_maps,
-                                 long long map_stride, int *d_err, cudaStream_t st) {
+                                 int n_tiles, int ext0, float *d_ws, const float *d_in,
+                                 float *d_out, int n_maps, long long map_stride, int *d_err,
+                                 cudaStream_t st) {
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
     static int n_sm = 0;
     if (n_sm == 0) {
@@ -324,16 +399,21 @@ cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_i
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (n_sm <= 0) n_sm = 1;
     }
-    const size_t smem = belt_mma_smem(w_cap);
-    cudaError_t e = cudaFuncSetAttribute(conv_belt_mma_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int groups = (n_maps + kN - 1) / kN;
-    int blocks = n_sm;  // one CTA per SM (shared memory and 64 TMEM columns each)
+    belt_tile_prep_kernel<<<4 * n_sm, 256, 0, st>>>(p, d_in, n_maps, map_stride, n_tiles, ext0,
+                                                    groups, d_ws);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = belt_mma_smem(w_cap);
+    e = cudaFuncSetAttribute(conv_belt_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    int blocks = n_sm;  // one CTA per SM (shared memory, 64 TMEM columns each)
     if (blocks > n_items) blocks = n_items;
     dim3 grid(blocks, groups);
-    conv_belt_mma_kernel<<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out, n_maps,
-                                                       map_stride, w_cap, d_err);
+    conv_belt_mma_kernel<<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_ws, n_tiles, ext0,
+                                                       groups, d_out, n_maps, map_stride, w_cap,
+                                                       d_err);
     return cudaGetLastError();
 }
 

@@ -117,9 +117,11 @@ cudaError_t launch_conv_belt(const ConvPlan &p, const int2 *d_items, int n_items
 int belt_mma_block();
 int belt_mma_maps();
 size_t belt_mma_smem(int w_cap);
+size_t belt_mma_workspace_floats(int n_belt, int n_tiles, int n_maps);
 cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_items, int w_cap,
-                                 const float *d_in, float *d_out, int n_maps,
-                                 long long map_stride, int *d_err, cudaStream_t st);
+                                 int n_tiles, int ext0, float *d_ws, const float *d_in,
+                                 float *d_out, int n_maps, long long map_stride, int *d_err,
+                                 cudaStream_t st);
 
 // Symmetric gather over northern rings (and the equator): each thread owns
 // one first-quarter position and writes its eight images; only output rings
@@ -171,6 +173,9 @@ struct ksc_split {
     int n_items_mma = 0;
     int w_cap = 0;                         // widest belt weight window
     int tensor = 0;                        // 0: tensor kernel for >= 16 maps, 1: never
+    int mma_ext0 = 0, mma_ntiles = 0;      // ring extension and K tiles per belt ring
+    float *d_ws = nullptr;                 // pre-tiled map stack (tensor path workspace)
+    size_t ws_floats = 0;
     int *d_err = nullptr;                  // device error flag (bounded waits)
     ksc::ConvPlan plan{};
 
