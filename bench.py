@@ -311,6 +311,9 @@ def run_ours(args, world, rank, local):
     multimap = None
     if world == 1 and not args.no_multimap and args.workload == "nside2048":
         multimap = run_multimap(K, torch, dev, stream, pk)
+    batch = None
+    if world == 1 and not args.no_batch and args.workload == "nside2048":
+        batch = run_batch(K, torch, dev, stream, big_split=sp)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -335,6 +338,7 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "multimap": multimap,
+        "batch": batch,
     }
     print(json.dumps(line), flush=True)
     sp.close()
@@ -389,6 +393,102 @@ def run_multimap(K, torch, dev, stream, pk):
                                      "issues 3 TF32 MMAs per product for FP32 accuracy"}}
 
 
+def _time_calls(fn, stream, torch, reps=3):
+    """Mean CUDA-event time (s) of fn() on `stream` after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_.record(stream)
+    for _ in range(reps):
+        fn()
+    b_.record(stream)
+    torch.cuda.synchronize()
+    return a_.elapsed_time(b_) / 1e3 / reps
+
+
+def run_batch(K, torch, dev, stream, big_split=None):
+    """Batched persistent launches (ksc_batch): (a) 64 maps at nside 1024, each with
+    its own least-squares split (FWHM uniform in [7, 30]', l_max 3071, l_cut 768,
+    theta_cut 240'); (b) a ragged batch of nside 256 / 512 / 1024 / 2048 maps.  Each
+    is autotuned, then timed as one graph-replayed batch run against the same
+    entries as serial single-map calls (maps/s)."""
+    from concurrent.futures import ThreadPoolExecutor
+    out = {}
+    lmax, lcut, tc = 3071, 768, 240.0 * ARC
+    fw = inputs.fwhm_draws(64, 7.0, 30.0, inputs.seed_for(4))
+    cl = inputs.cl_grf(lmax)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(8) as ex:  # ctypes releases the GIL during each fit
+        sps = list(ex.map(lambda f: K.make_split(inputs.gaussian_beam(lmax, f), 1024, lcut, tc,
+                                                 cl_in=cl), fw))
+    t_fit = time.perf_counter() - t0
+    pairs = [K.count_pairs(s) for s in sps]
+    npix = 12 * 1024 ** 2
+    xs = [torch.from_numpy(inputs.white_noise_map(1024, inputs.seed_for(4, 100 + i))
+                           .astype(np.float32)).to(dev) for i in range(64)]
+    ys = [torch.empty_like(x) for x in xs]
+    out["per_map_beams"] = _batch_case(K, torch, stream, sps, xs, ys, sum(pairs))
+    out["per_map_beams"].update({
+        "workload": "64 maps x nside 1024, per-map LSQ splits, FWHM U[7,30]', l_max 3071, "
+                    "l_cut 768, theta_cut 240'", "split_fit_s_total": round(t_fit, 1)})
+    del xs, ys
+    for s in sps:
+        s.close()
+    # ragged: 32 x nside 256 (40'), 16 x 512 (20'), 4 x 1024 (10'), 1 x 2048 (5')
+    ragged, xs = [], []
+    specs = [(256, 32, 40.0), (512, 16, 20.0), (1024, 4, 10.0)]
+    own = []
+    for ns, cnt, fwhm in specs:
+        lm = 2 * ns
+        sp = K.make_split(inputs.gaussian_beam(lm, fwhm * ARC), ns, ns // 2, 2.0 * fwhm * ARC * 8,
+                          cl_in=inputs.cl_grf(lm))
+        K.count_pairs(sp)
+        own.append(sp)
+        for i in range(cnt):
+            ragged.append(sp)
+            xs.append(torch.from_numpy(inputs.white_noise_map(ns, inputs.seed_for(4, 200 + len(xs)))
+                                       .astype(np.float32)).to(dev))
+    if big_split is not None:
+        ragged.append(big_split)
+        xs.append(torch.from_numpy(inputs.white_noise_map(2048, inputs.seed_for(4, 300))
+                                   .astype(np.float32)).to(dev))
+    ys = [torch.empty_like(x) for x in xs]
+    n_pairs = sum(K.split_info(s)["n_pairs"] for s in ragged)
+    out["ragged"] = _batch_case(K, torch, stream, ragged, xs, ys, n_pairs)
+    out["ragged"]["workload"] = ("32 x nside 256 (40'), 16 x 512 (20'), 4 x 1024 (10'), "
+                                 "1 x 2048 (5', the main split); theta_cut 16 x FWHM")
+    # small maps alone: where one launch per map leaves the GPU part-idle
+    n_small = 32
+    sm_specs = [s_ for s_ in ragged if s_ is own[0]][:n_small]
+    xs_s = xs[:n_small]
+    ys_s = [torch.empty_like(x) for x in xs_s]
+    out["small"] = _batch_case(K, torch, stream, sm_specs, xs_s, ys_s,
+                               n_small * K.split_info(own[0])["n_pairs"])
+    out["small"]["workload"] = "32 x nside 256 (40' beam, l_max 512, l_cut 128, theta_cut 640')"
+    for s in own:
+        s.close()
+    return out
+
+
+def _batch_case(K, torch, stream, splits, xs, ys, n_pairs):
+    n = len(splits)
+    t_serial = _time_calls(lambda: [K.conv_real(s, x, y) for s, x, y in zip(splits, xs, ys)],
+                           stream, torch)
+    with K.Batch(splits, use_graph=True) as b:
+        rep = b.autotune(xs, ys)
+        t_batch = _time_calls(lambda: b.run(xs, ys), stream, torch)
+        b.status()
+        info = b.info()
+    with K.Batch(splits, use_graph=False) as b:
+        t_nograph = _time_calls(lambda: b.run(xs, ys), stream, torch)
+    return {"maps": n, "pairs_per_run": n_pairs,
+            "maps_per_s_batch": n / t_batch, "maps_per_s_serial": n / t_serial,
+            "maps_per_s_batch_no_graph": n / t_nograph,
+            "pairs_per_s_batch": n_pairs / t_batch, "ms_batch": 1e3 * t_batch,
+            "ms_serial": 1e3 * t_serial, "launches_per_run": info["n_launches"],
+            "autotune": rep["groups"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +499,7 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multimap", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--workload", default="nside2048", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     WORKLOAD.clear()

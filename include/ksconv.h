@@ -167,11 +167,92 @@ int ksc_conv_real_multimap(const ksc_split *s, const float *d_in,
 /*
  * A ragged batch: n independent convolutions (each its own split, hence its
  * own nside, beam and theta_cut) in one call; splits, d_in and d_out are
- * host arrays of n entries.  Asynchronous.
+ * host arrays of n entries.  Runs a transient ksc_batch (below, without graph
+ * capture) and releases it before returning: synchronous on `stream`.  For
+ * repeated batches create a ksc_batch once and call ksc_batch_run.
  */
 int ksc_conv_real_batch(const ksc_split *const *splits,
                         const float *const *d_in, float *const *d_out, int n,
                         void *stream);
+
+/* ---- batched persistent launches, CUDA graphs, autotuned tiles --------- */
+/*
+ * A ksc_batch holds n entries, entry i = one map convolved with splits[i]
+ * (entries may repeat a split: a stack of maps under one kernel; or mix
+ * nside, beam and theta_cut: a ragged batch).  The work items of all entries
+ * are merged into one list per kernel and tile variant (entries in decreasing
+ * order of work, each entry's items longest first) and each list runs as ONE
+ * persistent launch whose CTAs claim items from a device counter (so short
+ * maps fill the tail of long ones).  With use_graph the launch sequence is
+ * captured once as a CUDA graph and replayed.  Results equal those of
+ * ksc_conv_real on each entry to FP32 rounding (the batch kernels are separate
+ * instantiations, free to contract multiply-adds differently, and the
+ * half-size gather tile regroups the FP32 partial sums); repeated runs of a
+ * batch are bitwise reproducible.
+ * The splits must outlive the batch.  Batches are not thread-safe: one run at
+ * a time per batch (runs of one batch on one stream are ordered).
+ */
+typedef struct ksc_batch ksc_batch; /* opaque, library-owned */
+
+typedef struct {
+    int use_graph;   /* 1 (default): capture the launches once as a CUDA graph
+                        and replay it; 0: enqueue the launches on each run   */
+    int per_sm_cap;  /* resident CTAs per SM; 0 (default) = occupancy limit  */
+} ksc_batch_opts;
+
+int ksc_batch_default_opts(ksc_batch_opts *opts);
+
+/* Build a batch (host work lists, device tables; synchronous).  Tile variants
+ * come from earlier ksc_batch_autotune results of this process for the same
+ * device, nside, lmax, table size and theta_cut, else a default (half-size
+ * belt items where a belt ring has at most 1040 pixels).
+ * Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_CUDA. */
+int ksc_batch_create(const ksc_split *const *splits, int n,
+                     const ksc_batch_opts *opts, ksc_batch **out);
+
+/* Convolve every entry: d_in[i], d_out[i] are device maps of entry i (host
+ * arrays of n pointers, same rules as ksc_conv_real).  Asynchronous on
+ * `stream`; the pointer table is re-uploaded only when it changed since the
+ * previous run.  Errors: KSC_ERR_ARG, KSC_ERR_CUDA. */
+int ksc_batch_run(ksc_batch *b, const float *const *d_in, float *const *d_out,
+                  void *stream);
+
+typedef struct {
+    int n_groups;              /* nside groups tuned (at most 8 reported)    */
+    int nside[8];
+    int belt_variant[8];       /* 0: 2080-output belt items, 1: 1040         */
+    int sym_variant[8];        /* 0: 128-class gather items, 1: 64           */
+    double ms_belt[8][2];      /* median launch time of each belt variant    */
+    double ms_sym[8][2];       /* median launch time of each gather variant  */
+} ksc_tune_report;
+
+/* The autotuner: for every nside group of the batch, time each tile variant
+ * of the belt kernel and of the symmetric gather on the given maps (a warm-up
+ * and three timed launches each, CUDA events on `stream`), keep the faster of
+ * each, rebuild the work lists, and remember the choice for later batches in
+ * this process.  Synchronous.  d_out holds no defined result afterwards (the
+ * gather adds into it repeatedly): run the batch again.  rep may be NULL. */
+int ksc_batch_autotune(ksc_batch *b, const float *const *d_in,
+                       float *const *d_out, void *stream, ksc_tune_report *rep);
+
+typedef struct {
+    int n_entries, n_splits, n_groups;
+    int n_items_belt, n_items_sym;  /* items over all persistent launches   */
+    int n_launches;                 /* kernel launches per run              */
+    int use_graph;
+    long long n_pairs;              /* in-disc pairs per run, or -1 when a
+                                       split has not counted its pairs      */
+    int group_nside[8], group_belt_variant[8], group_sym_variant[8];
+} ksc_batch_desc;
+
+int ksc_batch_info(const ksc_batch *b, ksc_batch_desc *out);
+
+/* Synchronize `stream` and report device-side errors raised by runs of this
+ * batch (as ksc_device_status does for a split); clears the flag. */
+int ksc_batch_status(ksc_batch *b, void *stream);
+
+/* Release a batch (NULL is a no-op); its runs must have completed. */
+void ksc_batch_free(ksc_batch *b);
 
 /*
  * End-to-end convenience: host map in, host map out (12 nside^2 floats each),

@@ -151,6 +151,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     // rounding differences between host and device acos
     const int seg = bc + max_nd + 6 * 13 + 16;
     s->seg_cap = (seg + 3) & ~3;
+    s->max_nd = max_nd;
     const bool belt_ok = s->n_items_belt > 0 && 12ull * s->seg_cap <= 200ull * 1024;
     s->path = o.path;
     if (!belt_ok && o.path == 0) {
@@ -195,6 +196,22 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                 }
                 pairs[(size_t)pair_base[r] + (q - range[r].x)] = pi;
             }
+        }
+    }
+
+    // Work per output pixel of each ring (window positions over its input
+    // rings), for ordering batched work longest first.
+    s->cost_belt.assign(nr, 0.0);
+    s->cost_sym.assign(nr, 0.0);
+    for (int r = 0; r < nr; ++r) {
+        const bool belt_r = r >= belt_lo && r <= belt_hi;
+        for (int q = range[r].x; q <= range[r].y; ++q) {
+            const ksc::PairInfo &pi = pairs[(size_t)pair_base[r] + (q - range[r].x)];
+            if (pi.hw < 0.0f) continue;
+            const double span = std::min(2.0 * pi.hw + 3.0, (double)g.len[q]);
+            const bool belt_q = q >= belt_lo && q <= belt_hi;
+            if (s->path == 0 && belt_r && belt_q) s->cost_belt[r] += span;
+            else s->cost_sym[r] += span;
         }
     }
 
@@ -515,14 +532,22 @@ int ksc_conv_real_batch(const ksc_split *const *splits, const float *const *d_in
                         float *const *d_out, int n, void *stream) {
     if (n < 0 || (n > 0 && (!splits || !d_in || !d_out)))
         return fail(KSC_ERR_ARG, "bad batch arrays");
+    if (n == 0) return KSC_OK;
     for (int i = 0; i < n; ++i) {
         int rc = check_maps(splits[i], d_in[i], d_out[i]);
         if (rc) return rc;
     }
-    for (int i = 0; i < n; ++i) {
-        int rc = ksc_conv_real(splits[i], d_in[i], d_out[i], stream);
-        if (rc) return rc;
-    }
+    ksc_batch_opts o;
+    ksc_batch_default_opts(&o);
+    o.use_graph = 0;
+    ksc_batch *b = nullptr;
+    int rc = ksc_batch_create(splits, n, &o, &b);
+    if (rc) return rc;
+    rc = ksc_batch_run(b, d_in, d_out, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    ksc_batch_free(b);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "batch synchronize");
     return KSC_OK;
 }
 

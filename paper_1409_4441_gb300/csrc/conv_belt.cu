@@ -22,6 +22,7 @@
 //   4. folds the FP32 ring partial sums into the totals with Kahan steps.
 // Every mbarrier wait is bounded; a wait that runs out raises a device error
 // flag and the kernel stops work instead of hanging.
+#include <algorithm>
 #include <cstdint>
 
 #include "ksc_device.cuh"
@@ -32,7 +33,7 @@ namespace {
 
 constexpr int kU = 13;          // outputs per thread (odd: conflict-free strides)
 constexpr int kThreads = 160;   // 5 warps
-constexpr int kChunk = kU * kThreads;
+constexpr int kChunk = kU * kThreads;  // outputs per item of the single-split kernel
 constexpr int kMaxWait = 1 << 22;   // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -104,161 +105,233 @@ __device__ __forceinline__ PairGeom pair_geom(const PairInfo &pi, int L, int tdi
     return g;
 }
 
-__global__ void __launch_bounds__(kThreads)
-conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
-                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
-                 int seg_cap, int *__restrict__ err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *seg0 = reinterpret_cast<float *>(smem_raw);
-    float *seg1 = seg0 + seg_cap;
-    float *wbuf = seg1 + seg_cap;  // seg_cap floats as well
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ PairGeom s_g[2];
-    __shared__ int s_abort;
-
+// One work item: outputs [k0, k0 + T kU) of belt ring r of one map.  The
+// shared buffers, barriers and their phases persist across items.  Returns
+// false when a bounded wait ran out (the error flag is set and any copy still
+// in flight has been waited for): the CTA must stop.
+template <int T>
+__device__ __forceinline__ bool belt_item(const ConvPlan &P, int r, int k0,
+                                          const float *__restrict__ m, float *__restrict__ o,
+                                          float *seg0, float *seg1, float *wbuf, uint64_t *bar,
+                                          PairGeom *s_g, int *s_abort, uint32_t &phase0,
+                                          uint32_t &phase1, int seg_cap, int *__restrict__ err) {
+    constexpr int kChunkT = kU * T;
     const int tid = threadIdx.x;
-    const float *m = in + (long long)blockIdx.y * map_stride;
-    float *o = out + (long long)blockIdx.y * map_stride;
+    const DevRing R = P.d_rings[r];
+    const int L = R.len;
+    const int2 rg = P.d_range[r];
+    const int q_lo = max(rg.x, P.belt_lo), q_hi = min(rg.y, P.belt_hi);
+    const int kb = tid * kU;  // first output (chunk-relative) of this thread
+    float sum[kU], comp[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) sum[u] = comp[u] = 0.0f;
 
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    uint32_t phase0 = 0u, phase1 = 0u;  // expected parity of bar[0], bar[1]
+    // issue the copy of input ring q into buffer b
+    const PairInfo *pinfo = P.d_pairs + P.d_pair_base[r] - rg.x;
+    auto issue = [&](int q, int b) {
+        const DevRing Q = P.d_rings[q];
+        PairGeom g = pair_geom(pinfo[q], L, R.phase - Q.phase, P.belt_c1h, P.belt_c1l);
+        s_g[b] = g;
+        if (g.empty) return;
+        // ring coordinates [a, a + n), a aligned down to 4 floats
+        int a = k0 + g.d0;
+        int n = kChunkT + g.nd - 1;
+        int a4 = a & ~3;  // floor to a multiple of 4 (also for negatives)
+        n += a - a4;
+        n = (n + 3) & ~3;
+        if (n > seg_cap) {  // never expected: the host sized seg_cap for every pair
+            atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
+            s_g[b].empty = true;
+            return;
+        }
+        float *dst = b ? seg1 : seg0;
+        const float *ring = m + Q.start;
+        uint32_t total = 4u * (uint32_t)n;
+        mbar_expect_tx(&bar[b], total);
+        int pos = a4, done = 0;
+        while (done < n) {
+            int pm = ((pos % L) + L) % L;
+            int len = min(n - done, L - pm);
+            bulk_g2s(dst + done, ring + pm, 4u * (uint32_t)len, &bar[b]);
+            done += len;
+            pos += len;
+        }
+    };
 
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int r = items[it].x, k0 = items[it].y;
-        const DevRing R = P.d_rings[r];
-        const int L = R.len;
-        const int2 rg = P.d_range[r];
-        const int q_lo = max(rg.x, P.belt_lo), q_hi = min(rg.y, P.belt_hi);
-        const int kb = tid * kU;  // first output (chunk-relative) of this thread
-        float sum[kU], comp[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) sum[u] = comp[u] = 0.0f;
-
-        // issue the copy of input ring q into buffer b
-        const PairInfo *pinfo = P.d_pairs + P.d_pair_base[r] - rg.x;
-        auto issue = [&](int q, int b) {
-            const DevRing Q = P.d_rings[q];
-            PairGeom g = pair_geom(pinfo[q], L, R.phase - Q.phase, P.belt_c1h, P.belt_c1l);
-            s_g[b] = g;
-            if (g.empty) return;
-            // ring coordinates [a, a + n), a aligned down to 4 floats
-            int a = k0 + g.d0;
-            int n = kChunk + g.nd - 1;
-            int a4 = a & ~3;       // floor to a multiple of 4 (also for negatives)
-            n += a - a4;
-            n = (n + 3) & ~3;
-            if (n > seg_cap) {  // never expected: the host sized seg_cap for every pair
-                atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
-                s_g[b].empty = true;
-                return;
+    if (tid == 0 && q_lo <= q_hi) issue(q_lo, 0);
+    int b = 0;
+    for (int q = q_lo; q <= q_hi; ++q, b ^= 1) {
+        __syncthreads();  // previous pair's buffers are free; s_g[b] visible
+        if (tid == 0 && q + 1 <= q_hi) issue(q + 1, b ^ 1);
+        const PairGeom g = s_g[b];
+        if (g.empty) continue;
+        // weights for this ring pair (zero outside the cut / exact window)
+        for (int j = tid; j < g.nd; j += T) {
+            const int D = g.d0 + j;
+            float wv = 0.0f;
+            if (D >= g.exact_lo && D <= g.exact_hi) {
+                const float mf = (float)(g.tdiff - 2 * D);
+                const float xh = mf * g.c1.h;
+                const float xl = fmaf(mf, g.c1.h, -xh) + mf * g.c1.l;
+                int ti;
+                float f;
+                if (chord_to_table(g.A, g.B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f))
+                    wv = hermite(__ldg(&P.d_tab[ti]), f);
             }
-            float *dst = b ? seg1 : seg0;
-            const float *ring = m + Q.start;
-            uint32_t total = 4u * (uint32_t)n;
-            mbar_expect_tx(&bar[b], total);
-            int pos = a4, done = 0;
-            while (done < n) {
-                int pm = ((pos % L) + L) % L;
-                int len = min(n - done, L - pm);
-                bulk_g2s(dst + done, ring + pm, 4u * (uint32_t)len, &bar[b]);
-                done += len;
-                pos += len;
-            }
-        };
-
-        if (tid == 0 && q_lo <= q_hi) issue(q_lo, 0);
-        int b = 0;
-        for (int q = q_lo; q <= q_hi; ++q, b ^= 1) {
-            __syncthreads();  // previous pair's buffers are free; s_g[b] visible
-            if (tid == 0 && q + 1 <= q_hi) issue(q + 1, b ^ 1);
-            const PairGeom g = s_g[b];
-            if (g.empty) continue;
-            // weights for this ring pair (zero outside the cut / exact window)
-            for (int j = tid; j < g.nd; j += kThreads) {
-                const int D = g.d0 + j;
-                float wv = 0.0f;
-                if (D >= g.exact_lo && D <= g.exact_hi) {
-                    const float mf = (float)(g.tdiff - 2 * D);
-                    const float xh = mf * g.c1.h;
-                    const float xl = fmaf(mf, g.c1.h, -xh) + mf * g.c1.l;
-                    int ti;
-                    float f;
-                    if (chord_to_table(g.A, g.B, sin_df(xh, xl), P.nint2, P.n_int, &ti, &f))
-                        wv = hermite(__ldg(&P.d_tab[ti]), f);
-                }
-                wbuf[j] = wv;
-            }
-            const bool ok = mbar_wait(&bar[b], b ? phase1 : phase0);
-            if (ok) {
-                if (b) phase1 ^= 1u; else phase0 ^= 1u;
-            } else {
-                s_abort = 1;
-            }
-            __syncthreads();
-            if (s_abort) break;
-            // sliding-window FFMA: acc[u] = sum_j w[j] * seg[off + kb + u + j]
-            const float *sg = (b ? seg1 : seg0) + ((k0 + g.d0) - ((k0 + g.d0) & ~3)) + kb;
-            float acc[kU], ring[kU];  // block (2 kU steps) and ring-pair partial sums
-#pragma unroll
-            for (int u = 0; u < kU; ++u) acc[u] = ring[u] = 0.0f;
-            float R0[2 * kU];
-#pragma unroll
-            for (int e = 0; e < kU - 1; ++e) R0[e] = sg[e];
-            for (int j0 = 0; j0 < g.nd; j0 += 2 * kU) {
-                // block A: values j0 .. j0 + 2kU - 2 live in R0[(v) % 2kU]
-#pragma unroll
-                for (int e = kU - 1; e < 2 * kU - 1; ++e) R0[e] = sg[j0 + e];
-#pragma unroll
-                for (int jj = 0; jj < kU; ++jj) {
-                    const float wv = wbuf[j0 + jj];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u) acc[u] = fmaf(wv, R0[u + jj], acc[u]);
-                }
-                // block B: values j0 + kU .. j0 + 3kU - 2 -> R0[(v - j0) % 2kU]
-#pragma unroll
-                for (int e = 2 * kU - 1; e < 3 * kU - 1; ++e) R0[e % (2 * kU)] = sg[j0 + e];
-#pragma unroll
-                for (int jj = 0; jj < kU; ++jj) {
-                    const float wv = wbuf[j0 + kU + jj];
-#pragma unroll
-                    for (int u = 0; u < kU; ++u)
-                        acc[u] = fmaf(wv, R0[(kU + u + jj) % (2 * kU)], acc[u]);
-                }
-                // values j0 + 2kU .. j0 + 3kU - 2 already sit at R0[0 .. kU-2]
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    ring[u] += acc[u];
-                    acc[u] = 0.0f;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const float y = ring[u] - comp[u];
-                const float t = sum[u] + y;
-                comp[u] = (t - sum[u]) - y;
-                sum[u] = t;
-            }
+            wbuf[j] = wv;
+        }
+        const bool ok = mbar_wait(&bar[b], b ? phase1 : phase0);
+        if (ok) {
+            if (b) phase1 ^= 1u; else phase0 ^= 1u;
+        } else {
+            *s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) {
-            if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
-            // wait (bounded) for any copy still in flight before leaving
-            mbar_wait(&bar[0], phase0);
-            mbar_wait(&bar[1], phase1);
-            return;
+        if (*s_abort) break;
+        // sliding-window FFMA: acc[u] = sum_j w[j] * seg[off + kb + u + j]
+        const float *sg = (b ? seg1 : seg0) + ((k0 + g.d0) - ((k0 + g.d0) & ~3)) + kb;
+        float acc[kU], ring[kU];  // block (2 kU steps) and ring-pair partial sums
+#pragma unroll
+        for (int u = 0; u < kU; ++u) acc[u] = ring[u] = 0.0f;
+        float R0[2 * kU];
+#pragma unroll
+        for (int e = 0; e < kU - 1; ++e) R0[e] = sg[e];
+        for (int j0 = 0; j0 < g.nd; j0 += 2 * kU) {
+            // block A: values j0 .. j0 + 2kU - 2 live in R0[(v) % 2kU]
+#pragma unroll
+            for (int e = kU - 1; e < 2 * kU - 1; ++e) R0[e] = sg[j0 + e];
+#pragma unroll
+            for (int jj = 0; jj < kU; ++jj) {
+                const float wv = wbuf[j0 + jj];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) acc[u] = fmaf(wv, R0[u + jj], acc[u]);
+            }
+            // block B: values j0 + kU .. j0 + 3kU - 2 -> R0[(v - j0) % 2kU]
+#pragma unroll
+            for (int e = 2 * kU - 1; e < 3 * kU - 1; ++e) R0[e % (2 * kU)] = sg[j0 + e];
+#pragma unroll
+            for (int jj = 0; jj < kU; ++jj) {
+                const float wv = wbuf[j0 + kU + jj];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    acc[u] = fmaf(wv, R0[(kU + u + jj) % (2 * kU)], acc[u]);
+            }
+            // values j0 + 2kU .. j0 + 3kU - 2 already sit at R0[0 .. kU-2]
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                ring[u] += acc[u];
+                acc[u] = 0.0f;
+            }
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int k = k0 + kb + u;
-            if (k < L) o[R.start + k] = sum[u] * P.domega;
+            const float y = ring[u] - comp[u];
+            const float t = sum[u] + y;
+            comp[u] = (t - sum[u]) - y;
+            sum[u] = t;
         }
     }
+    __syncthreads();
+    if (*s_abort) {
+        if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
+        // wait (bounded) for any copy still in flight before leaving
+        mbar_wait(&bar[0], phase0);
+        mbar_wait(&bar[1], phase1);
+        return false;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        const int k = k0 + kb + u;
+        if (k < L) o[R.start + k] = sum[u] * P.domega;
+    }
+    return true;
+}
+
+// Shared state of a belt CTA: three seg_cap-float buffers (two input segments,
+// the weight vector) in dynamic shared memory, two mbarriers.
+#define KSC_BELT_SHARED_STATE                                           \
+    extern __shared__ __align__(16) unsigned char smem_raw[];          \
+    float *seg0 = reinterpret_cast<float *>(smem_raw);                  \
+    float *seg1 = seg0 + seg_cap;                                       \
+    float *wbuf = seg1 + seg_cap;                                       \
+    __shared__ __align__(8) uint64_t bar[2];                            \
+    __shared__ PairGeom s_g[2];                                         \
+    __shared__ int s_abort;                                             \
+    if (threadIdx.x == 0) {                                             \
+        mbar_init(&bar[0], 1);                                          \
+        mbar_init(&bar[1], 1);                                          \
+        s_abort = 0;                                                    \
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); \
+    }                                                                   \
+    __syncthreads();                                                    \
+    uint32_t phase0 = 0u, phase1 = 0u;
+
+// One split, items assigned round-robin; grid.y runs over maps.
+template <int T>
+__global__ void __launch_bounds__(T)
+conv_belt_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_items,
+                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
+                 int seg_cap, int *__restrict__ err) {
+    KSC_BELT_SHARED_STATE
+    const float *m = in + (long long)blockIdx.y * map_stride;
+    float *o = out + (long long)blockIdx.y * map_stride;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        if (!belt_item<T>(P, items[it].x, items[it].y, m, o, seg0, seg1, wbuf, bar, s_g,
+                          &s_abort, phase0, phase1, seg_cap, err))
+            return;
+    }
+}
+
+// A batch of (split, map) entries: persistent CTAs claim items (entry, ring,
+// first pixel) from a global counter, in the order of the list (longest
+// first), until the list is exhausted.
+template <int T>
+__global__ void __launch_bounds__(T)
+conv_belt_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__restrict__ entries,
+                       const int4 *__restrict__ items, int n_items, int seg_cap,
+                       int *__restrict__ err, int *__restrict__ counter) {
+    KSC_BELT_SHARED_STATE
+    __shared__ int s_next;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous claim
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_next;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        const BatchEntry e = entries[w.x];
+        if (!belt_item<T>(plans[e.plan], w.y, w.z, e.in, e.out, seg0, seg1, wbuf, bar, s_g,
+                          &s_abort, phase0, phase1, seg_cap, err))
+            return;
+    }
+}
+
+#undef KSC_BELT_SHARED_STATE
+
+int sm_count() {
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    return n_sm;
+}
+
+template <class K>
+cudaError_t belt_grid(K kernel, int threads, size_t smem, int n_items, int per_sm_cap,
+                      int *blocks) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
+    if (per_sm < 1) per_sm = 1;
+    *blocks = std::min(sm_count() * per_sm, n_items);
+    return cudaSuccess;
 }
 
 } // namespace
@@ -269,26 +342,39 @@ cudaError_t launch_conv_belt(const ConvPlan &p, const int2 *d_items, int n_items
                              const float *d_in, float *d_out, int n_maps, long long map_stride,
                              int *d_err, cudaStream_t st) {
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (n_sm <= 0) n_sm = 1;
-    }
     const size_t smem = sizeof(float) * 3 * (size_t)seg_cap;
-    cudaError_t e = cudaFuncSetAttribute(conv_belt_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = 0;
+    cudaError_t e = belt_grid(conv_belt_kernel<kThreads>, kThreads, smem, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_belt_kernel, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int blocks = n_sm * per_sm;
-    if (blocks > n_items) blocks = n_items;
     dim3 grid(blocks, n_maps);
-    conv_belt_kernel<<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
-                                                   seg_cap, d_err);
+    conv_belt_kernel<kThreads><<<grid, kThreads, smem, st>>>(p, d_items, n_items, d_in, d_out,
+                                                             map_stride, seg_cap, d_err);
+    return cudaGetLastError();
+}
+
+int belt_variant_chunk(int variant) { return kU * (variant == 1 ? kThreads / 2 : kThreads); }
+
+cudaError_t launch_conv_belt_batch(int variant, const ConvPlan *d_plans,
+                                   const BatchEntry *d_entries, const int4 *d_items, int n_items,
+                                   int seg_cap, int per_sm_cap, int *d_err, int *d_counter,
+                                   cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * 3 * (size_t)seg_cap;
+    int blocks = 0;
+    cudaError_t e;
+    if (variant == 1) {
+        constexpr int T = kThreads / 2;
+        e = belt_grid(conv_belt_batch_kernel<T>, T, smem, n_items, per_sm_cap, &blocks);
+        if (e != cudaSuccess) return e;
+        conv_belt_batch_kernel<T><<<blocks, T, smem, st>>>(d_plans, d_entries, d_items, n_items,
+                                                           seg_cap, d_err, d_counter);
+    } else {
+        constexpr int T = kThreads;
+        e = belt_grid(conv_belt_batch_kernel<T>, T, smem, n_items, per_sm_cap, &blocks);
+        if (e != cudaSuccess) return e;
+        conv_belt_batch_kernel<T><<<blocks, T, smem, st>>>(d_plans, d_entries, d_items, n_items,
+                                                           seg_cap, d_err, d_counter);
+    }
     return cudaGetLastError();
 }
 

@@ -31,11 +31,15 @@
 namespace ksc {
 namespace {
 
-constexpr int kThreads = 128;   // one thread per reflection class
+constexpr int kThreads = 128;   // one thread per reflection class (single-split kernel)
 constexpr int kRingChunk = 32;  // ring-pair constants staged per pass
-constexpr int kSpan = 512;      // staged input positions per segment
 constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, reflected}
-constexpr int kStride = kSpan + 4;
+// A CTA of T threads stages 4 T input positions per segment, each image row
+// padded by 4 floats.
+template <int T> struct SymShape {
+    static constexpr int kSpan = 4 * T;
+    static constexpr int kStride = kSpan + 4;
+};
 
 struct SymRing {  // one (output ring, input ring) pair
     DF A, B, c;
@@ -78,10 +82,11 @@ __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
 }
 
 // Positions a..b of one staged segment (starting at s0) for one thread.
-template <bool MIRROR, bool SMALL>
+template <int T, bool MIRROR, bool SMALL>
 __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float *st,
                                            int s0, int a, int b, long long num, int L, bool refl,
                                            float *sum, float *comp) {
+    constexpr int kStride = SymShape<T>::kStride;
     const float step = (float)(2 * L);
     float part[kImg];
 #pragma unroll
@@ -129,18 +134,19 @@ __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, 
     for (int i = 0; i < kImg; ++i) kahan(&sum[i], &comp[i], part[i]);
 }
 
-template <bool MIRROR>
+template <int T, bool MIRROR>
 __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n_cls,
                                          bool skip_belt_inputs, bool add, int band_lo,
                                          int band_hi, const float *__restrict__ m,
                                          float *__restrict__ o, SymRing *sR, float *st) {
+    constexpr int kSpan = SymShape<T>::kSpan, kStride = SymShape<T>::kStride;
     const int tid = threadIdx.x;
     const DevRing R = P.d_rings[r];
     const int L = R.len, Q = L / 4, t = R.phase;
     const int2 rg = P.d_range[r];
     const int k = c0 + tid;
     const bool active = k < n_cls;
-    const int k_first = c0, k_last = min(c0 + kThreads, n_cls) - 1;
+    const int k_first = c0, k_last = min(c0 + T, n_cls) - 1;
     // reflection partner of k; none when it is k itself up to a quarter turn
     const int kb = Q - k - t;
     const bool refl = kb != k && kb != Q;
@@ -181,7 +187,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             window(k_last, t, L, g, &numx, &dummy, &U1);
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 __syncthreads();  // the previous segment is consumed
-                for (int j = tid; j < kSpan; j += kThreads) {
+                for (int j = tid; j < kSpan; j += T) {
                     const int kp = s0 + j;
                     const int idx = pmod(kp, L2);
                     const int idr = pmod(Q2 - kp - g.phase, L2);
@@ -204,9 +210,9 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 const int a = max(klo, s0), b = min(khi, s0 + kSpan - 1);
                 if (a > b) continue;
                 if (g.small)
-                    accumulate<MIRROR, true>(P, g, st, s0, a, b, num, L, refl, sum, comp);
+                    accumulate<T, MIRROR, true>(P, g, st, s0, a, b, num, L, refl, sum, comp);
                 else
-                    accumulate<MIRROR, false>(P, g, st, s0, a, b, num, L, refl, sum, comp);
+                    accumulate<T, MIRROR, false>(P, g, st, s0, a, b, num, L, refl, sum, comp);
             }
         }
     }
@@ -239,27 +245,81 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
+// One work item: classes [k0, k0 + T) of northern ring `ring` of one map.
+template <int T>
+__device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0, int belt_split,
+                                             int band_lo, int band_hi, const float *m, float *o,
+                                             SymRing *sR, float *st) {
+    const int eq = (P.nrings - 1) / 2;  // the equator ring, its own mirror image
+    const DevRing R = P.d_rings[ring];
+    const int Q = R.len / 4;
+    const int n_cls = R.phase ? (Q + 1) / 2 : Q / 2 + 1;  // reflection classes
+    const bool belt = ring >= P.belt_lo && ring <= P.belt_hi;
+    const bool add = belt_split && belt;
+    if (ring == eq)
+        sym_item<T, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+    else
+        sym_item<T, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+}
+
+// One split, items assigned round-robin; grid.y runs over maps.
+template <int T, int MIN_BLOCKS>
+__global__ void __launch_bounds__(T, MIN_BLOCKS)
 conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
                 int belt_split, int band_lo, int band_hi) {
     __shared__ SymRing sR[kRingChunk];
-    __shared__ __align__(16) float st[kImg * kStride];
+    __shared__ __align__(16) float st[kImg * SymShape<T>::kStride];
     const float *m = in + (long long)blockIdx.y * map_stride;
     float *o = out + (long long)blockIdx.y * map_stride;
-    const int eq = (P.nrings - 1) / 2;  // the equator ring, its own mirror image
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        const DevRing R = P.d_rings[w.ring];
-        const int Q = R.len / 4;
-        const int n_cls = R.phase ? (Q + 1) / 2 : Q / 2 + 1;  // reflection classes
-        const bool belt = w.ring >= P.belt_lo && w.ring <= P.belt_hi;
-        const bool add = belt_split && belt;
-        if (w.ring == eq)
-            sym_item<false>(P, w.ring, w.k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
-        else
-            sym_item<true>(P, w.ring, w.k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+        sym_dispatch<T>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st);
     }
+}
+
+// A batch of (split, map) entries: persistent CTAs claim items (entry, ring,
+// first class) from a global counter in list order (longest first).
+template <int T, int MIN_BLOCKS>
+__global__ void __launch_bounds__(T, MIN_BLOCKS)
+conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__restrict__ entries,
+                      const int4 *__restrict__ items, int n_items, int *__restrict__ counter) {
+    __shared__ SymRing sR[kRingChunk];
+    __shared__ __align__(16) float st[kImg * SymShape<T>::kStride];
+    __shared__ int s_next;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous claim
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_next;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        const BatchEntry e = entries[w.x];
+        const ConvPlan &P = plans[e.plan];
+        sym_dispatch<T>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st);
+    }
+}
+
+int sm_count_sym() {
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (n_sm <= 0) n_sm = 1;
+    }
+    return n_sm;
+}
+
+template <class K>
+cudaError_t sym_grid(K kernel, int threads, int n_items, int per_sm_cap, int *blocks) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
+    if (per_sm < 1) per_sm = 1;
+    *blocks = n_items < sm_count_sym() * per_sm ? n_items : sm_count_sym() * per_sm;
+    return cudaSuccess;
 }
 
 } // namespace
@@ -273,26 +333,40 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
                             const float *d_in, float *d_out, int n_maps, long long map_stride,
                             int belt_split, int band_lo, int band_hi, cudaStream_t st) {
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (n_sm <= 0) n_sm = 1;
-    }
-    int per_sm = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_sym_kernel, kThreads, 0);
+    int blocks = 0;
+    cudaError_t e = sym_grid(conv_sym_kernel<kThreads, 3>, kThreads, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int blocks = n_sm * per_sm;
-    if (blocks > n_items) blocks = n_items;
     dim3 grid(blocks, n_maps);
-    conv_sym_kernel<<<grid, kThreads, 0, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
-                                               belt_split, band_lo, band_hi);
+    conv_sym_kernel<kThreads, 3><<<grid, kThreads, 0, st>>>(p, d_items, n_items, d_in, d_out,
+                                                           map_stride, belt_split, band_lo,
+                                                           band_hi);
     return cudaGetLastError();
 }
 
 int sym_chunk() { return kThreads; }
+
+int sym_variant_chunk(int variant) { return variant == 1 ? kThreads / 2 : kThreads; }
+
+cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
+                                  const BatchEntry *d_entries, const int4 *d_items, int n_items,
+                                  int per_sm_cap, int *d_counter, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    int blocks = 0;
+    cudaError_t e;
+    if (variant == 1) {
+        constexpr int T = kThreads / 2;
+        e = sym_grid(conv_sym_batch_kernel<T, 6>, T, n_items, per_sm_cap, &blocks);
+        if (e != cudaSuccess) return e;
+        conv_sym_batch_kernel<T, 6><<<blocks, T, 0, st>>>(d_plans, d_entries, d_items, n_items,
+                                                          d_counter);
+    } else {
+        constexpr int T = kThreads;
+        e = sym_grid(conv_sym_batch_kernel<T, 3>, T, n_items, per_sm_cap, &blocks);
+        if (e != cudaSuccess) return e;
+        conv_sym_batch_kernel<T, 3><<<blocks, T, 0, st>>>(d_plans, d_entries, d_items, n_items,
+                                                          d_counter);
+    }
+    return cudaGetLastError();
+}
 
 } // namespace ksc

@@ -134,6 +134,30 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
                             long long map_stride, int belt_split, int band_lo,
                             int band_hi, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Batched persistent launches (csrc/batch.cpp).  An entry is one map convolved
+// with one split; items are int4 {entry, ring, first pixel or class, 0}.
+// Variant 0 / 1 selects the full / half block size of a kernel (the autotuned
+// tile shape): belt items span belt_variant_chunk(v) outputs, symmetric items
+// sym_variant_chunk(v) reflection classes.  CTAs claim items from *d_counter,
+// which must be zero at launch.  per_sm_cap > 0 caps the resident CTAs per SM.
+// ---------------------------------------------------------------------------
+struct BatchEntry {
+    const float *in;
+    float *out;
+    int plan;        // index into the batch's ConvPlan array
+    int belt_split;  // 1: the belt kernel wrote this entry's belt-belt part
+};
+int belt_variant_chunk(int variant);
+int sym_variant_chunk(int variant);
+cudaError_t launch_conv_belt_batch(int variant, const ConvPlan *d_plans,
+                                   const BatchEntry *d_entries, const int4 *d_items, int n_items,
+                                   int seg_cap, int per_sm_cap, int *d_err, int *d_counter,
+                                   cudaStream_t st);
+cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
+                                  const BatchEntry *d_entries, const int4 *d_items, int n_items,
+                                  int per_sm_cap, int *d_counter, cudaStream_t st);
+
 // Record the message returned by ksc_last_error() on this thread.
 void set_last_error(const std::string &msg);
 
@@ -169,6 +193,8 @@ struct ksc_split {
     int n_items_belt = 0;
     std::vector<int> ring_first_belt;
     int seg_cap = 0;
+    int max_nd = 0;                        // widest circulant weight window (belt pairs)
+    std::vector<double> cost_belt, cost_sym; // per ring: window positions per output pixel
     int2 *d_items_mma = nullptr;           // 128-output belt blocks for the tensor kernel
     int n_items_mma = 0;
     int w_cap = 0;                         // widest belt weight window

@@ -18,9 +18,11 @@ ARCMIN = np.pi / (180.0 * 60.0)
 DEG = np.pi / 180.0
 
 
-def seed_for(config: int, index: int = 0) -> int:
-    """Seed recipe: 1409 + 100 * config + map index."""
-    return 1409 + 100 * config + index
+def seed_for(family: int, index: int = 0) -> int:
+    """Seed recipe: 1409 + 100 * family + map index, family = 1 plain nside-64
+    convolution, 2 nside-512 split, 3 nside-2048 split, 4 nside-1024 map stacks
+    and ragged batches, 5 surrogate training and the nside-4096 map (0: smoke)."""
+    return 1409 + 100 * family + index
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -95,12 +97,12 @@ def perturbed_coeffs(base, rel: float, seed: int) -> np.ndarray:
 
 # Workload recipes (sizes of the paper's Planck-resolution case, Sec. 2-3).
 WORKLOADS = {
-    "c1": dict(nside=64, lmax=191, fwhm=2.0 * DEG, theta_cut=6.0 * DEG, mode="none",
+    "plain_nside64": dict(nside=64, lmax=191, fwhm=2.0 * DEG, theta_cut=6.0 * DEG, mode="none",
                map="white"),
-    "c2": dict(nside=512, lmax=1535, fwhm=20.0 * ARCMIN, lcut=256, mode="lsq", map="grf"),
-    "c3": dict(nside=2048, lmax=4096, fwhm=5.0 * ARCMIN, lcut=1024, theta_cut=240.0 * ARCMIN,
+    "split_nside512": dict(nside=512, lmax=1535, fwhm=20.0 * ARCMIN, lcut=256, mode="lsq", map="grf"),
+    "planck_nside2048": dict(nside=2048, lmax=4096, fwhm=5.0 * ARCMIN, lcut=1024, theta_cut=240.0 * ARCMIN,
                mode="lsq", map="grf"),
-    "c4": dict(nside=1024, lmax=3071, n_maps=64, fwhm_lo=7.0, fwhm_hi=30.0, mode="lsq",
+    "multimap_nside1024": dict(nside=1024, lmax=3071, n_maps=64, fwhm_lo=7.0, fwhm_hi=30.0, mode="lsq",
                map="grf"),
-    "c5": dict(nside=4096, lmax=8192, fwhm=3.0 * ARCMIN, mode="lsq", map="grf"),
+    "surrogate_nside4096": dict(nside=4096, lmax=8192, fwhm=3.0 * ARCMIN, mode="lsq", map="grf"),
 }

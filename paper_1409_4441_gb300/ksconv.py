@@ -39,6 +39,8 @@ EXPORTS = [
     "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_conv_real_multimap_stage",
     "ksc_count_pairs", "ksc_device_status",
     "ksc_free_split", "ksc_build_table_noalloc",
+    "ksc_batch_default_opts", "ksc_batch_create", "ksc_batch_run", "ksc_batch_autotune",
+    "ksc_batch_info", "ksc_batch_status", "ksc_batch_free",
     "ksc_status_string", "ksc_last_error",
 ]
 
@@ -58,6 +60,25 @@ class Desc(ctypes.Structure):
                 ("sigma_rms", ctypes.c_double), ("frac_error", ctypes.c_double),
                 ("n_pairs", ctypes.c_longlong), ("n_pairs_belt", ctypes.c_longlong),
                 ("path", ctypes.c_int)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("use_graph", ctypes.c_int), ("per_sm_cap", ctypes.c_int)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int), ("nside", ctypes.c_int * 8),
+                ("belt_variant", ctypes.c_int * 8), ("sym_variant", ctypes.c_int * 8),
+                ("ms_belt", (ctypes.c_double * 2) * 8), ("ms_sym", (ctypes.c_double * 2) * 8)]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_entries", ctypes.c_int), ("n_splits", ctypes.c_int),
+                ("n_groups", ctypes.c_int), ("n_items_belt", ctypes.c_int),
+                ("n_items_sym", ctypes.c_int), ("n_launches", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("n_pairs", ctypes.c_longlong),
+                ("group_nside", ctypes.c_int * 8), ("group_belt_variant", ctypes.c_int * 8),
+                ("group_sym_variant", ctypes.c_int * 8)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -81,6 +102,13 @@ _sig = {
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
     "ksc_build_table_noalloc": [_vp, _i, _d, _i, _vp, _vp],
+    "ksc_batch_default_opts": [ctypes.POINTER(BatchOpts)],
+    "ksc_batch_create": [_vp, _i, ctypes.POINTER(BatchOpts), ctypes.POINTER(_vp)],
+    "ksc_batch_run": [_vp, _vp, _vp, _vp],
+    "ksc_batch_autotune": [_vp, _vp, _vp, _vp, ctypes.POINTER(TuneReport)],
+    "ksc_batch_info": [_vp, ctypes.POINTER(BatchDesc)],
+    "ksc_batch_status": [_vp, _vp],
+    "ksc_batch_free": [_vp],
     "ksc_status_string": [_i],
     "ksc_last_error": [],
 }
@@ -89,6 +117,7 @@ for _name, _args in _sig.items():
     _f.argtypes = _args
     _f.restype = _i
 _lib.ksc_free_split.restype = None
+_lib.ksc_batch_free.restype = None
 _lib.ksc_status_string.restype = ctypes.c_char_p
 _lib.ksc_last_error.restype = ctypes.c_char_p
 
@@ -292,3 +321,73 @@ def build_table_noalloc(d_c, lmax: int, theta_cut: float, n_intervals: int, d_ta
                                         n_intervals, _dptr_typed(d_table, "float32"),
                                         _stream(stream)), "ksc_build_table_noalloc")
     return d_table
+
+
+class Batch:
+    """A ksc_batch: entries (split, map) run as persistent launches, optionally
+    replayed as a CUDA graph.  Keeps its splits alive."""
+
+    def __init__(self, splits, use_graph: bool = True, per_sm_cap: int = 0):
+        self._splits = list(splits)
+        n = len(self._splits)
+        o = BatchOpts()
+        _check(_lib.ksc_batch_default_opts(ctypes.byref(o)), "ksc_batch_default_opts")
+        o.use_graph = 1 if use_graph else 0
+        o.per_sm_cap = int(per_sm_cap)
+        hs = (_vp * n)(*[s.handle for s in self._splits])
+        h = _vp()
+        _check(_lib.ksc_batch_create(hs, n, ctypes.byref(o), ctypes.byref(h)), "ksc_batch_create")
+        self._h = h.value
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("batch already freed")
+        return self._h
+
+    def _ptrs(self, d_ins, d_outs):
+        n = len(self._splits)
+        if len(d_ins) != n or len(d_outs) != n:
+            raise ValueError(f"expected {n} input and output maps")
+        return (_vp * n)(*[_dptr(t) for t in d_ins]), (_vp * n)(*[_dptr(t) for t in d_outs])
+
+    def run(self, d_ins, d_outs, stream=None):
+        ins, outs = self._ptrs(d_ins, d_outs)
+        _check(_lib.ksc_batch_run(self.handle, ins, outs, _stream(stream)), "ksc_batch_run")
+        return d_outs
+
+    def autotune(self, d_ins, d_outs, stream=None) -> dict:
+        ins, outs = self._ptrs(d_ins, d_outs)
+        r = TuneReport()
+        _check(_lib.ksc_batch_autotune(self.handle, ins, outs, _stream(stream), ctypes.byref(r)),
+               "ksc_batch_autotune")
+        return {"groups": [{"nside": r.nside[g], "belt_variant": r.belt_variant[g],
+                            "sym_variant": r.sym_variant[g],
+                            "ms_belt": [r.ms_belt[g][0], r.ms_belt[g][1]],
+                            "ms_sym": [r.ms_sym[g][0], r.ms_sym[g][1]]}
+                           for g in range(r.n_groups)]}
+
+    def info(self) -> dict:
+        d = BatchDesc()
+        _check(_lib.ksc_batch_info(self.handle, ctypes.byref(d)), "ksc_batch_info")
+        out = {f: getattr(d, f) for f, _ in BatchDesc._fields_ if not f.startswith("group_")}
+        out["groups"] = [{"nside": d.group_nside[g], "belt_variant": d.group_belt_variant[g],
+                          "sym_variant": d.group_sym_variant[g]} for g in range(min(d.n_groups, 8))]
+        return out
+
+    def status(self, stream=None):
+        _check(_lib.ksc_batch_status(self.handle, _stream(stream)), "ksc_batch_status")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ksc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
