@@ -221,9 +221,10 @@ typedef struct {
     int n_groups;              /* nside groups tuned (at most 8 reported)    */
     int nside[8];
     int belt_variant[8];       /* 0: 2080-output belt items, 1: 1040         */
-    int sym_variant[8];        /* 0: 128-class gather items, 1: 64           */
+    int sym_variant[8];        /* 0: 128-class gather items, 1: 64, 2: 64
+                                  classes on paired lanes (128 threads)      */
     double ms_belt[8][2];      /* median launch time of each belt variant    */
-    double ms_sym[8][2];       /* median launch time of each gather variant  */
+    double ms_sym[8][3];       /* median launch time of each gather variant  */
 } ksc_tune_report;
 
 /* The autotuner: for every nside group of the batch, time each tile variant

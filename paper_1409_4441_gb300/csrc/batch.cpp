@@ -14,11 +14,12 @@
 //
 // The tile variants are the full and half block size of each kernel (belt:
 // 2080 or 1040 outputs per item; symmetric gather: 128 or 64 reflection
-// classes per item).  Half blocks suit short rings (a 1024-pixel belt ring
-// fills only half of a 2080-output item).  The autotuner times both variants
-// of both kernels on every nside group of the batch, with the caller's maps,
-// keeps the faster of each, and caches the choice per (device, nside, l_max,
-// table size, theta_cut) for the rest of the process.
+// classes per item) and, for the gather, paired lanes (two lanes per class,
+// 64 classes per 128-thread item).  Half blocks suit short rings (a 1024-pixel
+// belt ring fills only half of a 2080-output item).  The autotuner times every
+// variant of both kernels on every nside group of the batch, with the caller's
+// maps, keeps the fastest of each, and caches the choice per (device, nside,
+// l_max, table size, theta_cut) for the rest of the process.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -127,7 +128,7 @@ void build_items(const ksc_batch *b, const std::vector<int> &sel,
     };
     *n_belt = *n_sym = 0;
     for (int kind = 0; kind < 2; ++kind) {
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < (kind == 0 ? 2 : ksc::sym_variants()); ++v) {
             // per entry: its items, longest first; entries ordered by total cost
             std::vector<std::pair<double, std::vector<Costed>>> per_entry;
             int seg_cap = 0;
@@ -417,8 +418,10 @@ int ksc_batch_autotune(ksc_batch *b, const float *const *d_in, float *const *d_o
         for (int i = 0; i < b->n; ++i)
             if (b->group_of[i] == (int)gi && b->splits[i]->path == 0) sel.push_back(i);
         if (sel.empty()) continue;
-        double ms[2][2] = {{0, 0}, {0, 0}};  // [kind][variant]
-        for (int v = 0; v < 2 && rc == KSC_OK; ++v) {
+        const int nv_sym = ksc::sym_variants();
+        double ms[2][3] = {{0, 0, 0}, {0, 0, 0}};  // [kind][variant]
+        for (int v = 0; v < nv_sym && rc == KSC_OK; ++v) {
+            // belt variants 0, 1 and gather variants 0 .. nv_sym - 1 (no belt beyond 1)
             std::vector<std::pair<int, int>> vars(b->nsides.size(), std::make_pair(v, v));
             std::vector<int4> items;
             std::vector<Launch> launches;
@@ -439,6 +442,7 @@ int ksc_batch_autotune(ksc_batch *b, const float *const *d_in, float *const *d_o
             } else {
                 b->d_counters = d_ctr;
                 for (size_t li = 0; li < launches.size() && rc == KSC_OK; ++li) {
+                    if (launches[li].kind == 0 && v > 1) continue;
                     std::vector<Launch> one(1, launches[li]);
                     std::vector<float> t;
                     for (int rep_i = 0; rep_i < 4 && rc == KSC_OK; ++rep_i) {
@@ -462,8 +466,10 @@ int ksc_batch_autotune(ksc_batch *b, const float *const *d_in, float *const *d_o
         }
         if (rc) break;
         const bool has_belt = ms[0][0] > 0.0 || ms[0][1] > 0.0;
-        std::pair<int, int> best(has_belt && ms[0][1] < ms[0][0] ? 1 : 0,
-                                 ms[1][1] < ms[1][0] ? 1 : 0);
+        int best_sym = 0;
+        for (int v = 1; v < nv_sym; ++v)
+            if (ms[1][v] < ms[1][best_sym]) best_sym = v;
+        std::pair<int, int> best(has_belt && ms[0][1] < ms[0][0] ? 1 : 0, best_sym);
         b->variants[gi] = best;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -474,10 +480,8 @@ int ksc_batch_autotune(ksc_batch *b, const float *const *d_in, float *const *d_o
             rep->nside[gi] = b->nsides[gi];
             rep->belt_variant[gi] = best.first;
             rep->sym_variant[gi] = best.second;
-            for (int v = 0; v < 2; ++v) {
-                rep->ms_belt[gi][v] = ms[0][v];
-                rep->ms_sym[gi][v] = ms[1][v];
-            }
+            for (int v = 0; v < 2; ++v) rep->ms_belt[gi][v] = ms[0][v];
+            for (int v = 0; v < 3; ++v) rep->ms_sym[gi][v] = ms[1][v];
         }
     }
     cudaEventDestroy(e0);

@@ -25,21 +25,32 @@
 // dphi / 2 = N pi / (2 L L') (ksc_device.cuh); K_r comes from the cubic
 // Hermite table through the L1 cache.  FP32 partial sums over 32 positions are
 // Kahan-folded into the totals.
+//
+// Paired lanes (tile variant 2): two adjacent lanes own one class.  Each
+// evaluates two of every four kernel weights, the pair swaps them with one
+// shuffle, and each lane accumulates one hemisphere (eight images).  The work
+// per class is the same; the accumulators per thread halve, so more warps fit
+// on an SM to hide the latency of the double-float chains.
 #include "ksc_device.cuh"
 #include "ksc_internal.h"
 
 namespace ksc {
 namespace {
 
-constexpr int kThreads = 128;   // one thread per reflection class (single-split kernel)
 constexpr int kRingChunk = 32;  // ring-pair constants staged per pass
 constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, reflected}
-// A CTA of T threads stages 4 T input positions per segment, each image row
-// padded by 4 floats.
-template <int T> struct SymShape {
-    static constexpr int kSpan = 4 * T;
-    static constexpr int kStride = kSpan + 4;
+// Tile shape: T threads, LANES lanes per reflection class (1, or 2 for paired
+// lanes), SPAN staged input positions per segment (each image row padded by 4
+// floats), MINB resident CTAs per SM the register budget is set for.
+template <int T_, int LANES_, int SPAN_, int MINB_> struct SymShape {
+    static constexpr int T = T_, LANES = LANES_, kSpan = SPAN_, MINB = MINB_;
+    static constexpr int kStride = SPAN_ + 4;
+    static constexpr int kClasses = T_ / LANES_;      // classes per item
+    static constexpr int kImgT = kImg / LANES_;       // images per thread
 };
+using ShapeFull = SymShape<128, 1, 512, 3>;   // variant 0
+using ShapeHalf = SymShape<64, 1, 256, 6>;    // variant 1
+using ShapePair = SymShape<128, 2, 384, 5>;   // variant 2
 
 struct SymRing {  // one (output ring, input ring) pair
     DF A, B, c;
@@ -81,78 +92,119 @@ __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
     *sum = tt;
 }
 
-// Positions a..b of one staged segment (starting at s0) for one thread.
-template <int T, bool MIRROR, bool SMALL>
-__device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float *st,
-                                           int s0, int a, int b, long long num, int L, bool refl,
-                                           float *sum, float *comp) {
-    constexpr int kStride = SymShape<T>::kStride;
+// Row of thread image i in the staged block: images are ordered
+// [direct q0..q3 | mirror direct q0..q3 | reflected q0..q3 | mirror reflected];
+// with paired lanes, lane h (0 north, 1 south) takes rows 4h..4h+3 and 8+4h..
+__device__ __forceinline__ int img_row(int i, int lanes, int h) {
+    if (lanes == 1) return i;
+    return i < 4 ? 4 * h + i : 8 + 4 * h + (i - 4);
+}
+
+// The four kernel weights of quad kq (positions kq .. kq + 3; zero outside
+// [a, b] and beyond the cut).  With paired lanes each lane evaluates two and
+// the pair swaps them.  Straight-line code: the evaluations interleave.
+template <class S, bool SMALL>
+__device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing &g, int kq, int a,
+                                               int b, long long num, int L, int h,
+                                               unsigned pair_mask) {
+    const float N0 = (float)(num - 2LL * kq * L);  // exact integer below 2^24
     const float step = (float)(2 * L);
-    float part[kImg];
+    float w[4];
+    constexpr int NE = 4 / S::LANES;  // weights evaluated by this lane
 #pragma unroll
-    for (int i = 0; i < kImg; ++i) part[i] = 0.0f;
+    for (int ee = 0; ee < NE; ++ee) {
+        const int e = S::LANES == 2 ? 2 * h + ee : ee;
+        const float Nf = N0 - (float)e * step;
+        const float xh = Nf * g.c.h;
+        const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
+        const DF sn = SMALL ? sin_df_small(xh, xl) : sin_df(xh, xl);
+        const int kp = kq + e;
+        int ti;
+        float f;
+        const bool in = chord_to_table_sel(g.A, g.B, sn, P.nint2, &ti, &f);
+        const float wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
+        w[ee] = (in && kp >= a && kp <= b) ? wv : 0.0f;
+    }
+    if constexpr (S::LANES == 2) {  // swap halves with the partner lane
+        const float o0 = __shfl_xor_sync(pair_mask, w[0], 1);
+        const float o1 = __shfl_xor_sync(pair_mask, w[1], 1);
+        if (h == 0) { w[2] = o0; w[3] = o1; }
+        else { w[2] = w[0]; w[3] = w[1]; w[0] = o0; w[1] = o1; }
+    }
+    return make_float4(w[0], w[1], w[2], w[3]);
+}
+
+// Positions a..b of one staged segment (starting at s0) for one thread.  The
+// loop is software-pipelined: the weights of the next quad are evaluated
+// while the current quad's weights feed the FFMAs, so the long double-float
+// chains overlap the multiply-adds.
+template <class S, bool MIRROR, bool SMALL>
+__device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float *st,
+                                           int s0, int a, int b, long long num, int L,
+                                           float *sum, float *comp) {
+    constexpr int kStride = S::kStride, NI = S::kImgT;
+    const int h = S::LANES == 2 ? (threadIdx.x & 1) : 0;
+    const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1);
+    const bool idle = S::LANES == 2 && !MIRROR && h == 1;  // no south images on the equator
+    float part[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) part[i] = 0.0f;
     int nq = 0;
-    for (int kq = s0 + ((a - s0) & ~3); kq <= b; kq += 4) {
-        const float N0 = (float)(num - 2LL * kq * L);  // exact integer below 2^24
-        float w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float Nf = N0 - (float)e * step;
-            const float xh = Nf * g.c.h;
-            const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
-            const DF sn = SMALL ? sin_df_small(xh, xl) : sin_df(xh, xl);
-            const int kp = kq + e;
-            int ti;
-            float f;
-            w[e] = 0.0f;
-            if (kp >= a && kp <= b && chord_to_table_padded(g.A, g.B, sn, P.nint2, &ti, &f))
-                w[e] = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
-        }
+    int kq = s0 + ((a - s0) & ~3);
+    if (kq > b) return;
+    float4 wc = quad_weights<S, SMALL>(P, g, kq, a, b, num, L, h, pair_mask);
+    for (; kq <= b; kq += 4) {
+        // next quad's weights (past b they are zero and unused)
+        const float4 wn = quad_weights<S, SMALL>(P, g, kq + 4, a, b, num, L, h, pair_mask);
         const int j = kq - s0;
+        if (!idle) {
 #pragma unroll
-        for (int img = 0; img < kImg; ++img) {
-            if (!MIRROR && (img & 4)) continue;
-            if (img >= 8 && !refl) continue;
-            const float4 v = *reinterpret_cast<const float4 *>(st + img * kStride + j);
-            float p = part[img];
-            p = fmaf(w[0], v.x, p);
-            p = fmaf(w[1], v.y, p);
-            p = fmaf(w[2], v.z, p);
-            p = fmaf(w[3], v.w, p);
-            part[img] = p;
+            for (int i = 0; i < NI; ++i) {
+                const int img = img_row(i, S::LANES, h);
+                if (S::LANES == 1 && !MIRROR && (img & 4)) continue;
+                const float4 v = *reinterpret_cast<const float4 *>(st + img * kStride + j);
+                float p = part[i];
+                p = fmaf(wc.x, v.x, p);
+                p = fmaf(wc.y, v.y, p);
+                p = fmaf(wc.z, v.z, p);
+                p = fmaf(wc.w, v.w, p);
+                part[i] = p;
+            }
         }
+        wc = wn;
         if (++nq == 8) {  // fold every 32 positions
             nq = 0;
 #pragma unroll
-            for (int i = 0; i < kImg; ++i) {
+            for (int i = 0; i < NI; ++i) {
                 kahan(&sum[i], &comp[i], part[i]);
                 part[i] = 0.0f;
             }
         }
     }
 #pragma unroll
-    for (int i = 0; i < kImg; ++i) kahan(&sum[i], &comp[i], part[i]);
+    for (int i = 0; i < NI; ++i) kahan(&sum[i], &comp[i], part[i]);
 }
 
-template <int T, bool MIRROR>
+template <class S, bool MIRROR>
 __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n_cls,
                                          bool skip_belt_inputs, bool add, int band_lo,
                                          int band_hi, const float *__restrict__ m,
                                          float *__restrict__ o, SymRing *sR, float *st) {
-    constexpr int kSpan = SymShape<T>::kSpan, kStride = SymShape<T>::kStride;
+    constexpr int T = S::T, kSpan = S::kSpan, kStride = S::kStride, NI = S::kImgT;
     const int tid = threadIdx.x;
+    const int h = S::LANES == 2 ? (tid & 1) : 0;  // paired lanes: hemisphere
     const DevRing R = P.d_rings[r];
     const int L = R.len, Q = L / 4, t = R.phase;
     const int2 rg = P.d_range[r];
-    const int k = c0 + tid;
+    const int k = c0 + tid / S::LANES;
     const bool active = k < n_cls;
-    const int k_first = c0, k_last = min(c0 + T, n_cls) - 1;
+    const int k_first = c0, k_last = min(c0 + S::kClasses, n_cls) - 1;
     // reflection partner of k; none when it is k itself up to a quarter turn
     const int kb = Q - k - t;
     const bool refl = kb != k && kb != Q;
-    float sum[kImg], comp[kImg];
+    float sum[NI], comp[NI];
 #pragma unroll
-    for (int i = 0; i < kImg; ++i) sum[i] = comp[i] = 0.0f;
+    for (int i = 0; i < NI; ++i) sum[i] = comp[i] = 0.0f;
 
     for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
         const int nq = min(kRingChunk, rg.y - q0 + 1);
@@ -186,8 +238,10 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             window(k_first, t, L, g, &numx, &U0, &dummy);
             window(k_last, t, L, g, &numx, &dummy, &U1);
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
+                // positions this segment needs (the union ends at U1)
+                const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
                 __syncthreads();  // the previous segment is consumed
-                for (int j = tid; j < kSpan; j += T) {
+                for (int j = tid; j < span; j += T) {
                     const int kp = s0 + j;
                     const int idx = pmod(kp, L2);
                     const int idr = pmod(Q2 - kp - g.phase, L2);
@@ -209,10 +263,12 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 if (!active) continue;
                 const int a = max(klo, s0), b = min(khi, s0 + kSpan - 1);
                 if (a > b) continue;
+                // (classes without a reflection partner accumulate the reflected
+                // images too; those sums are never written)
                 if (g.small)
-                    accumulate<T, MIRROR, true>(P, g, st, s0, a, b, num, L, refl, sum, comp);
+                    accumulate<S, MIRROR, true>(P, g, st, s0, a, b, num, L, sum, comp);
                 else
-                    accumulate<T, MIRROR, false>(P, g, st, s0, a, b, num, L, refl, sum, comp);
+                    accumulate<S, MIRROR, false>(P, g, st, s0, a, b, num, L, sum, comp);
             }
         }
     }
@@ -228,16 +284,26 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int kq = kk + qq * Q;
-                const float vn = sum[8 * c + qq] * P.domega;
-                if (wn) {
-                    if (add) o[R.start + kq] += vn;
-                    else o[R.start + kq] = vn;
-                }
-                if constexpr (MIRROR) {
-                    const float vs = sum[8 * c + 4 + qq] * P.domega;
-                    if (ws) {
-                        if (add) o[start_s + kq] += vs;
-                        else o[start_s + kq] = vs;
+                if (S::LANES == 1) {
+                    const float vn = sum[8 * c + qq] * P.domega;
+                    if (wn) {
+                        if (add) o[R.start + kq] += vn;
+                        else o[R.start + kq] = vn;
+                    }
+                    if constexpr (MIRROR) {
+                        const float vs = sum[8 * c + 4 + qq] * P.domega;
+                        if (ws) {
+                            if (add) o[start_s + kq] += vs;
+                            else o[start_s + kq] = vs;
+                        }
+                    }
+                } else {  // lane h writes its hemisphere
+                    const float v = sum[4 * c + qq] * P.domega;
+                    const bool wr = h == 0 ? wn : ws;
+                    const int base = h == 0 ? R.start : start_s;
+                    if (wr) {
+                        if (add) o[base + kq] += v;
+                        else o[base + kq] = v;
                     }
                 }
             }
@@ -245,8 +311,8 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
     }
 }
 
-// One work item: classes [k0, k0 + T) of northern ring `ring` of one map.
-template <int T>
+// One work item: classes [k0, k0 + S::kClasses) of northern ring `ring` of one map.
+template <class S>
 __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0, int belt_split,
                                              int band_lo, int band_hi, const float *m, float *o,
                                              SymRing *sR, float *st) {
@@ -257,35 +323,35 @@ __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0
     const bool belt = ring >= P.belt_lo && ring <= P.belt_hi;
     const bool add = belt_split && belt;
     if (ring == eq)
-        sym_item<T, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
     else
-        sym_item<T, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
 }
 
 // One split, items assigned round-robin; grid.y runs over maps.
-template <int T, int MIN_BLOCKS>
-__global__ void __launch_bounds__(T, MIN_BLOCKS)
+template <class S>
+__global__ void __launch_bounds__(S::T, S::MINB)
 conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
                 int belt_split, int band_lo, int band_hi) {
     __shared__ SymRing sR[kRingChunk];
-    __shared__ __align__(16) float st[kImg * SymShape<T>::kStride];
+    __shared__ __align__(16) float st[kImg * S::kStride];
     const float *m = in + (long long)blockIdx.y * map_stride;
     float *o = out + (long long)blockIdx.y * map_stride;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        sym_dispatch<T>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st);
+        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st);
     }
 }
 
 // A batch of (split, map) entries: persistent CTAs claim items (entry, ring,
 // first class) from a global counter in list order (longest first).
-template <int T, int MIN_BLOCKS>
-__global__ void __launch_bounds__(T, MIN_BLOCKS)
+template <class S>
+__global__ void __launch_bounds__(S::T, S::MINB)
 conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__restrict__ entries,
                       const int4 *__restrict__ items, int n_items, int *__restrict__ counter) {
     __shared__ SymRing sR[kRingChunk];
-    __shared__ __align__(16) float st[kImg * SymShape<T>::kStride];
+    __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
     for (;;) {
         __syncthreads();  // every thread has read the previous claim
@@ -296,7 +362,7 @@ conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__re
         const int4 w = items[it];
         const BatchEntry e = entries[w.x];
         const ConvPlan &P = plans[e.plan];
-        sym_dispatch<T>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st);
+        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st);
     }
 }
 
@@ -333,40 +399,49 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
                             const float *d_in, float *d_out, int n_maps, long long map_stride,
                             int belt_split, int band_lo, int band_hi, cudaStream_t st) {
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
+    using S = ShapeFull;
     int blocks = 0;
-    cudaError_t e = sym_grid(conv_sym_kernel<kThreads, 3>, kThreads, n_items, 0, &blocks);
+    cudaError_t e = sym_grid(conv_sym_kernel<S>, S::T, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
     dim3 grid(blocks, n_maps);
-    conv_sym_kernel<kThreads, 3><<<grid, kThreads, 0, st>>>(p, d_items, n_items, d_in, d_out,
-                                                           map_stride, belt_split, band_lo,
-                                                           band_hi);
+    conv_sym_kernel<S><<<grid, S::T, 0, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
+                                             belt_split, band_lo, band_hi);
     return cudaGetLastError();
 }
 
-int sym_chunk() { return kThreads; }
+int sym_chunk() { return ShapeFull::kClasses; }
 
-int sym_variant_chunk(int variant) { return variant == 1 ? kThreads / 2 : kThreads; }
+int sym_variants() { return 3; }
+
+int sym_variant_chunk(int variant) {
+    return variant == 2 ? ShapePair::kClasses
+                        : (variant == 1 ? ShapeHalf::kClasses : ShapeFull::kClasses);
+}
+
+template <class S>
+cudaError_t sym_batch_launch(const ConvPlan *d_plans, const BatchEntry *d_entries,
+                             const int4 *d_items, int n_items, int per_sm_cap, int *d_counter,
+                             cudaStream_t st) {
+    int blocks = 0;
+    cudaError_t e = sym_grid(conv_sym_batch_kernel<S>, S::T, n_items, per_sm_cap, &blocks);
+    if (e != cudaSuccess) return e;
+    conv_sym_batch_kernel<S><<<blocks, S::T, 0, st>>>(d_plans, d_entries, d_items, n_items,
+                                                      d_counter);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
                                   const BatchEntry *d_entries, const int4 *d_items, int n_items,
                                   int per_sm_cap, int *d_counter, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    int blocks = 0;
-    cudaError_t e;
-    if (variant == 1) {
-        constexpr int T = kThreads / 2;
-        e = sym_grid(conv_sym_batch_kernel<T, 6>, T, n_items, per_sm_cap, &blocks);
-        if (e != cudaSuccess) return e;
-        conv_sym_batch_kernel<T, 6><<<blocks, T, 0, st>>>(d_plans, d_entries, d_items, n_items,
-                                                          d_counter);
-    } else {
-        constexpr int T = kThreads;
-        e = sym_grid(conv_sym_batch_kernel<T, 3>, T, n_items, per_sm_cap, &blocks);
-        if (e != cudaSuccess) return e;
-        conv_sym_batch_kernel<T, 3><<<blocks, T, 0, st>>>(d_plans, d_entries, d_items, n_items,
-                                                          d_counter);
-    }
-    return cudaGetLastError();
+    if (variant == 2)
+        return sym_batch_launch<ShapePair>(d_plans, d_entries, d_items, n_items, per_sm_cap,
+                                           d_counter, st);
+    if (variant == 1)
+        return sym_batch_launch<ShapeHalf>(d_plans, d_entries, d_items, n_items, per_sm_cap,
+                                           d_counter, st);
+    return sym_batch_launch<ShapeFull>(d_plans, d_entries, d_items, n_items, per_sm_cap,
+                                       d_counter, st);
 }
 
 } // namespace ksc

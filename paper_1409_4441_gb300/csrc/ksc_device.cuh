@@ -126,6 +126,32 @@ __device__ __forceinline__ bool chord_to_table_padded(DF A, DF B, DF s, float ni
     return true;
 }
 
+// Branch-free chord_to_table_padded: always returns a valid table position
+// (beyond the cut, D is clamped to the cut, u = n_int, the padded entry) and
+// reports whether the pair lies within the cut.  Straight-line code lets the
+// compiler interleave several independent evaluations.
+__device__ __forceinline__ bool chord_to_table_sel(DF A, DF B, DF s, float nint2, int *i_out,
+                                                   float *f_out) {
+    const float s2h = s.h * s.h;
+    const float s2l = fmaf(2.0f * s.h, s.l, fmaf(s.h, s.h, -s2h));
+    const float ph = B.h * s2h;
+    const float pl = fmaf(B.h, s2h, -ph) + fmaf(B.h, s2l, B.l * s2h);
+    const float dh0 = A.h + ph;
+    const float bp = dh0 - A.h;
+    const float e = (A.h - (dh0 - bp)) + (ph - bp);
+    const float dl0 = e + A.l + pl;
+    const bool in = dh0 <= nint2;
+    const float dh = in ? dh0 : nint2;
+    const float dl = in ? dl0 : 0.0f;
+    const float r = rsqrtf(fmaxf(dh, 1e-30f));
+    const float uh = dh * r;
+    const float ul = (fmaf(-uh, uh, dh) + dl) * (0.5f * r);
+    const float t = (uh - 0.5f) + 12582912.0f;
+    *i_out = __float_as_int(t) - 0x4B400000;
+    *f_out = (uh - (t - 12582912.0f)) + ul;
+    return in;
+}
+
 __device__ __forceinline__ float hermite(const float4 c, float f) {
     return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
 }

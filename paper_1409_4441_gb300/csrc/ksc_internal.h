@@ -137,9 +137,10 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
 // ---------------------------------------------------------------------------
 // Batched persistent launches (csrc/batch.cpp).  An entry is one map convolved
 // with one split; items are int4 {entry, ring, first pixel or class, 0}.
-// Variant 0 / 1 selects the full / half block size of a kernel (the autotuned
-// tile shape): belt items span belt_variant_chunk(v) outputs, symmetric items
-// sym_variant_chunk(v) reflection classes.  CTAs claim items from *d_counter,
+// The tile variant selects a kernel's block shape (the autotuned tile): belt
+// variant 0 / 1 = full / half block (belt_variant_chunk(v) outputs per item);
+// gather variant 0 / 1 = full / half block, 2 = paired lanes
+// (sym_variant_chunk(v) reflection classes per item).  CTAs claim items from *d_counter,
 // which must be zero at launch.  per_sm_cap > 0 caps the resident CTAs per SM.
 // ---------------------------------------------------------------------------
 struct BatchEntry {
@@ -148,7 +149,8 @@ struct BatchEntry {
     int plan;        // index into the batch's ConvPlan array
     int belt_split;  // 1: the belt kernel wrote this entry's belt-belt part
 };
-int belt_variant_chunk(int variant);
+int belt_variant_chunk(int variant);  // variants 0, 1
+int sym_variants();                   // number of gather variants
 int sym_variant_chunk(int variant);
 cudaError_t launch_conv_belt_batch(int variant, const ConvPlan *d_plans,
                                    const BatchEntry *d_entries, const int4 *d_items, int n_items,

@@ -69,7 +69,7 @@ class BatchOpts(ctypes.Structure):
 class TuneReport(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int), ("nside", ctypes.c_int * 8),
                 ("belt_variant", ctypes.c_int * 8), ("sym_variant", ctypes.c_int * 8),
-                ("ms_belt", (ctypes.c_double * 2) * 8), ("ms_sym", (ctypes.c_double * 2) * 8)]
+                ("ms_belt", (ctypes.c_double * 2) * 8), ("ms_sym", (ctypes.c_double * 3) * 8)]
 
 
 class BatchDesc(ctypes.Structure):
@@ -364,7 +364,7 @@ class Batch:
         return {"groups": [{"nside": r.nside[g], "belt_variant": r.belt_variant[g],
                             "sym_variant": r.sym_variant[g],
                             "ms_belt": [r.ms_belt[g][0], r.ms_belt[g][1]],
-                            "ms_sym": [r.ms_sym[g][0], r.ms_sym[g][1]]}
+                            "ms_sym": [r.ms_sym[g][v] for v in range(3)]}
                            for g in range(r.n_groups)]}
 
     def info(self) -> dict:
