@@ -76,7 +76,18 @@ typedef struct {
     int tensor;        /* 0 (default): ksc_conv_real_multimap runs belt ring
                           pairs on the tcgen05 tensor cores (TF32 x3, FP32
                           accumulate) when n_maps >= 16; 1: FFMA kernels only */
+    int cut_continuity; /* LSQ mode: how the fitted real-space kernel meets the
+                          cut (the truncation "to a limit theta_cut" of Sec. 2):
+                          KSC_CUT_C1 (0, default) value and slope vanish at
+                          theta_cut; KSC_CUT_C0 value only; KSC_CUT_FREE the
+                          fit is unconstrained and K_r may jump at the cut
+                          (a jump leaves a pixel-sum error on smooth maps of
+                          about |K_r(theta_cut)| x boundary pixels)          */
 } ksc_split_opts;
+
+#define KSC_CUT_C1 0
+#define KSC_CUT_C0 1
+#define KSC_CUT_FREE 2
 
 /* Fill *opts with the defaults listed above. */
 int ksc_default_opts(ksc_split_opts *opts);

@@ -171,8 +171,34 @@ def real_space_basis(lmax: int, theta_cut: float, oversample: int = 2):
     return zj, wj, Pj, A
 
 
+def continuity_map(zj, wj, Pj, theta_cut: float, order: int):
+    """Elimination matrix T (x = T t) that makes the truncated real-space kernel
+    K_r = sum_j x_j f_j vanish at theta_cut (order 1), with zero slope there too
+    (order 2).  Reading of Sec. 2's truncation "to a limit theta_cut": the
+    compact kernel reaches zero continuously at the cut (a jump there makes the
+    pixel sum of Sec. 3 miss or double-count boundary pixels).  The unknowns at
+    the `order` nodes nearest the cut are expressed through the others:
+    C_E x_E + C_F x_F = 0, rows of C = f_j(z_cut) and f_j'(z_cut), each f_j
+    evaluated as the Legendre sum of its coefficients 2 pi w_j P_l(z_j)."""
+    nz = zj.size
+    if order <= 0 or nz <= order:
+        return np.eye(nz), np.arange(nz)
+    zc = np.cos(theta_cut)
+    g, h = np.empty(nz), np.empty(nz)
+    for j in range(nz):
+        v, d = legendre_sum(2.0 * np.pi * wj[j] * Pj[j], zc, deriv=True)
+        g[j], h[j] = v[0], d[0]
+    E = np.argsort(np.abs(zj - zc))[:order]
+    F = np.setdiff1d(np.arange(nz), E)
+    Cm = np.vstack([g, h])[:order]
+    T = np.zeros((nz, F.size))
+    T[F, np.arange(F.size)] = 1.0
+    T[E, :] = -np.linalg.solve(Cm[:, E], Cm[:, F])
+    return T, F
+
+
 def split_lsq(K, lcut: int, theta_cut: float, cl_in=None, oversample: int = 2,
-              rcond: float = 1e-6):
+              rcond: float = 1e-6, continuity: int = 2):
     """Eq. 3: A^T W A x = A^T W K_l, solved by SVD (Sec. 2).
 
     x = [Khat_l (l <= l_cut); Khat_theta (z_cut values)] (Eq. 4); A = [delta | P]
@@ -180,7 +206,9 @@ def split_lsq(K, lcut: int, theta_cut: float, cl_in=None, oversample: int = 2,
     the input spectrum of Eq. 2).  As in Sec. 2, the SVD is taken of the normal
     matrix A^T W A of Eq. 3 (columns of W^{1/2} A scaled to unit norm, so the
     cut is scale-free) and singular values below rcond (1e-6) times the largest
-    are dropped.
+    are dropped.  With continuity 1 (2) the real-space kernel is constrained to
+    vanish (with zero slope) at theta_cut by eliminating the unknowns nearest
+    the cut (continuity_map); 0 leaves it free.
 
     Returns a dict with k_harm (l <= l_cut), x (real-space unknowns), the
     Legendre coefficients c_real (l <= lmax) of the real-space part before
@@ -191,10 +219,11 @@ def split_lsq(K, lcut: int, theta_cut: float, cl_in=None, oversample: int = 2,
     ell = np.arange(lmax + 1)
     C = np.ones(lmax + 1) if cl_in is None else np.asarray(cl_in, dtype=np.float64)
     zj, wj, Pj, A = real_space_basis(lmax, theta_cut, oversample)
+    T, _ = continuity_map(zj, wj, Pj, theta_cut, continuity)
     nh = lcut + 1
-    M = np.zeros((lmax + 1, nh + zj.size))
+    M = np.zeros((lmax + 1, nh + T.shape[1]))
     M[np.arange(nh), np.arange(nh)] = 1.0
-    M[:, nh:] = A
+    M[:, nh:] = A @ T
     sw = np.sqrt((2 * ell + 1) * C)
     B = sw[:, None] * M
     b = sw * K
@@ -207,7 +236,7 @@ def split_lsq(K, lcut: int, theta_cut: float, cl_in=None, oversample: int = 2,
     keep = s > rcond * s[0]
     y = (Vt[keep].T @ ((U[:, keep].T @ rhs) / s[keep])) / cn
     k_harm = y[:nh]
-    x = y[nh:]
+    x = T @ y[nh:]
     c_real = 2.0 * np.pi * (Pj.T @ (wj * x))
     K_tilde = M @ y
     return dict(k_harm=k_harm, x=x, z_nodes=zj, w_nodes=wj, A=A, c_real=c_real,
@@ -260,7 +289,8 @@ def t_cpu_eq8(lcut, lmax):
 
 
 def scan_split(K, theta_grid_rad, bound: float = 1e-5, cl_in=None, alpha: float = 5.0,
-               t_gpu=None, t_cpu=None, oversample: int = 2, rcond: float = 1e-6):
+               t_gpu=None, t_cpu=None, oversample: int = 2, rcond: float = 1e-6,
+               continuity: int = 2):
     """Sec. 2 scanning strategy: linear scan over theta_cut; for each, a binary
     search for the smallest l_cut meeting the Eq. 6 bound; then the pair with the
     least wall time max(t_gpu, t_cpu) (the two halves run concurrently, Fig. 1).
@@ -273,7 +303,7 @@ def scan_split(K, theta_grid_rad, bound: float = 1e-5, cl_in=None, alpha: float 
     t_cpu = t_cpu or (lambda lc: float(t_cpu_eq8(lc, lmax)))
 
     def err(lc, th):
-        sp = split_lsq(K, lc, th, cl_in, oversample, rcond)
+        sp = split_lsq(K, lc, th, cl_in, oversample, rcond, continuity)
         return frac_error(K, sp["K_tilde"], cl_in, alpha)
 
     table = []

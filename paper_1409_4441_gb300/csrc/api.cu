@@ -305,6 +305,8 @@ ksc_split_opts resolve_opts(const ksc_split_opts *opts) {
         if (!(o.alpha > 0.0)) o.alpha = 5.0;
         if (o.path != 1) o.path = 0;
         if (o.tensor != 1) o.tensor = 0;
+        if (o.cut_continuity < KSC_CUT_C1 || o.cut_continuity > KSC_CUT_FREE)
+            o.cut_continuity = KSC_CUT_C1;
     }
     return o;
 }
@@ -396,6 +398,7 @@ int ksc_default_opts(ksc_split_opts *opts) {
     opts->n_intervals = 0;
     opts->path = 0;
     opts->tensor = 0;
+    opts->cut_continuity = KSC_CUT_C1;
     return KSC_OK;
 }
 
@@ -419,8 +422,10 @@ int ksc_make_split(const double *b_l, int lmax, int nside, int l_cut, double the
         if (o.mode == KSC_SPLIT_LSQ) {
             ksc::FitResult fr;
             std::string msg;
+            const int n_con = o.cut_continuity == KSC_CUT_FREE ? 0
+                              : (o.cut_continuity == KSC_CUT_C0 ? 1 : 2);
             rc = ksc::fit_split_lsq(b_l, lmax, l_cut, theta_cut, cl_in, o.oversample,
-                                    o.svd_rcond, &fr, &msg);
+                                    o.svd_rcond, n_con, &fr, &msg);
             if (rc) { release(s); return fail(rc, msg); }
             s->l_cut = l_cut;
             s->k_harm = fr.k_harm; s->c_real = fr.c_real; s->k_tilde = fr.k_tilde;

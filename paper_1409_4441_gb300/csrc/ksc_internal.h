@@ -48,8 +48,10 @@ struct FitResult {
     int n_unknowns = 0, n_kept = 0;
 };
 // Returns KSC_OK or an error code; *msg receives a reason on failure.
+// n_constraints: 0 free real-space kernel, 1 K_r(theta_cut) = 0, 2 also
+// dK_r/dz(theta_cut) = 0 (ksc_split_opts.cut_continuity).
 int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
-                  const double *cl_in, int oversample, double rcond,
+                  const double *cl_in, int oversample, double rcond, int n_constraints,
                   FitResult *out, std::string *msg);
 
 // Eq. 2 and Eq. 6 of a fitted kernel.

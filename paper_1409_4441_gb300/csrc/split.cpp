@@ -130,8 +130,8 @@ double frac_error_eq6(const double *K, const double *Kt, const double *cl, int l
 }
 
 int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
-                  const double *cl_in, int oversample, double rcond, FitResult *out,
-                  std::string *msg) {
+                  const double *cl_in, int oversample, double rcond, int n_constraints,
+                  FitResult *out, std::string *msg) {
     const int L = lmax + 1;
     const double zc = std::cos(theta_cut);
 
@@ -215,28 +215,88 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
     std::vector<double>().swap(Pq);
     std::vector<double>().swap(F);
 
+    // Continuity at the cut (reading of Sec. 2's truncation "to a limit
+    // theta_cut"): the real-space kernel K_r = sum_j x_j f_j is made to vanish
+    // at z_cut (n_constraints >= 1) with zero slope there (2) by eliminating the
+    // unknowns at the nodes nearest the cut (the last ones, nodes descend to
+    // z_cut): C_E x_E + C_F x_F = 0 with rows f_j(z_cut), f_j'(z_cut).  A jump
+    // at the cut would make the pixel sum over-/under-count boundary pixels.
+    const int nc = std::min(std::max(n_constraints, 0), std::max(nz - 1, 0));
+    const int nf = nz - nc;
+    // x = T t: T is nz x nf, identity on the free nodes 0..nf-1
+    std::vector<double> TE((size_t)nc * nf, 0.0);  // rows of T for the eliminated nodes
+    if (nc > 0) {
+        std::vector<double> pc(L), dc(L);
+        pc[0] = 1.0; dc[0] = 0.0;
+        if (lmax >= 1) { pc[1] = zc; dc[1] = 1.0; }
+        for (int l = 1; l < lmax; ++l) {
+            pc[l + 1] = ((2.0 * l + 1.0) * zc * pc[l] - (double)l * pc[l - 1]) / (double)(l + 1);
+            dc[l + 1] = dc[l - 1] + (2.0 * l + 1.0) * pc[l];
+        }
+        std::vector<double> cg(nz, 0.0), ch(nz, 0.0);  // f_j(z_cut), f_j'(z_cut)
+        for (int l = 0; l < L; ++l)
+            for (int j = 0; j < nz; ++j) {
+                cg[j] += G[(size_t)l * nz + j] * pc[l];
+                ch[j] += G[(size_t)l * nz + j] * dc[l];
+            }
+        if (nc == 1) {
+            const double ge = cg[nz - 1];
+            if (!(std::fabs(ge) > 0.0)) {
+                *msg = "continuity constraint is singular at this theta_cut";
+                return KSC_ERR_SVD;
+            }
+            for (int f = 0; f < nf; ++f) TE[f] = -cg[f] / ge;
+        } else {
+            // [g_a g_b; h_a h_b] x_E = -[g_F; h_F] x_F, a = nz-2, b = nz-1
+            const double a11 = cg[nz - 2], a12 = cg[nz - 1], a21 = ch[nz - 2], a22 = ch[nz - 1];
+            const double det = a11 * a22 - a12 * a21;
+            const double scale = std::fabs(a11 * a22) + std::fabs(a12 * a21);
+            if (!(std::fabs(det) > 1e-12 * scale)) {
+                *msg = "continuity constraint is singular at this theta_cut";
+                return KSC_ERR_SVD;
+            }
+            for (int f = 0; f < nf; ++f) {
+                const double rg = -cg[f], rh = -ch[f];
+                TE[f] = (rg * a22 - a12 * rh) / det;
+                TE[(size_t)nf + f] = (a11 * rh - a21 * rg) / det;
+            }
+        }
+    }
+    // Columns of the constrained operator: A T (L x nf)
+    std::vector<double> AT((size_t)L * nf);
+    for (int l = 0; l < L; ++l) {
+        const double *row = &A[(size_t)l * nz];
+        double *o = &AT[(size_t)l * nf];
+        for (int f = 0; f < nf; ++f) {
+            double v = row[f];
+            for (int e = 0; e < nc; ++e) v += row[nf + e] * TE[(size_t)e * nf + f];
+            o[f] = v;
+        }
+    }
+
     // Reduced weighted system on rows l > l_cut, unit-norm columns.
     const int m = lmax - l_cut;
-    std::vector<double> Bm((size_t)nz * m);  // column-major m x nz
-    std::vector<double> bv(m), cn(nz, 0.0);
+    std::vector<double> Bm((size_t)nf * m);  // column-major m x nf
+    std::vector<double> bv(m), cn(nf, 0.0);
     for (int i = 0; i < m; ++i) {
         int l = l_cut + 1 + i;
         double sw = std::sqrt((2.0 * l + 1.0) * (cl_in ? cl_in[l] : 1.0));
         bv[i] = sw * K[l];
-        for (int j = 0; j < nz; ++j) Bm[(size_t)j * m + i] = sw * A[(size_t)l * nz + j];
+        for (int j = 0; j < nf; ++j) Bm[(size_t)j * m + i] = sw * AT[(size_t)l * nf + j];
     }
-    for (int j = 0; j < nz; ++j) {
+    std::vector<double>().swap(AT);
+    for (int j = 0; j < nf; ++j) {
         double s = 0;
         for (int i = 0; i < m; ++i) s += Bm[(size_t)j * m + i] * Bm[(size_t)j * m + i];
         cn[j] = s > 0 ? std::sqrt(s) : 1.0;
         for (int i = 0; i < m; ++i) Bm[(size_t)j * m + i] /= cn[j];
     }
 
-    // Householder QR when tall: R (p x nz, column-major), c = Q^T b.
+    // Householder QR when tall: R (p x nf, column-major), c = Q^T b.
     int p = m;
     std::vector<double> R, cvec;
-    if (m > nz) {
-        for (int j = 0; j < nz; ++j) {
+    if (m > nf) {
+        for (int j = 0; j < nf; ++j) {
             double *col = &Bm[(size_t)j * m];
             double nrm = 0;
             for (int i = j; i < m; ++i) nrm += col[i] * col[i];
@@ -248,7 +308,7 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
             double vn = 0;
             for (double e : v) vn += e * e;
             if (vn == 0.0) continue;
-            for (int jj = j; jj < nz; ++jj) {
+            for (int jj = j; jj < nf; ++jj) {
                 double *cc = &Bm[(size_t)jj * m];
                 double d = 0;
                 for (int i = j; i < m; ++i) d += v[i - j] * cc[i];
@@ -260,11 +320,11 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
             d = 2.0 * d / vn;
             for (int i = j; i < m; ++i) bv[i] -= d * v[i - j];
         }
-        p = nz;
-        R.assign((size_t)nz * nz, 0.0);
-        for (int j = 0; j < nz; ++j)
-            for (int i = 0; i <= j; ++i) R[(size_t)j * nz + i] = Bm[(size_t)j * m + i];
-        cvec.assign(bv.begin(), bv.begin() + nz);
+        p = nf;
+        R.assign((size_t)nf * nf, 0.0);
+        for (int j = 0; j < nf; ++j)
+            for (int i = 0; i <= j; ++i) R[(size_t)j * nf + i] = Bm[(size_t)j * m + i];
+        cvec.assign(bv.begin(), bv.begin() + nf);
     } else {
         R = Bm;
         cvec = bv;
@@ -272,13 +332,13 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
     std::vector<double>().swap(Bm);
 
     std::vector<double> V;
-    if (!jacobi_svd(p, nz, R, V)) {
+    if (!jacobi_svd(p, nf, R, V)) {
         *msg = "one-sided Jacobi SVD did not converge";
         return KSC_ERR_SVD;
     }
-    std::vector<double> sig(nz);
+    std::vector<double> sig(nf);
     double smax = 0;
-    for (int j = 0; j < nz; ++j) {
+    for (int j = 0; j < nf; ++j) {
         double s = 0;
         for (int k = 0; k < p; ++k) s += R[(size_t)j * p + k] * R[(size_t)j * p + k];
         sig[j] = std::sqrt(s);
@@ -287,18 +347,23 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
     // The cut of Sec. 2 applies to the singular values of the normal matrix
     // A^T W A (Eq. 3), the squares of those of W^{1/2} A.
     const double cut = std::sqrt(rcond) * smax;
-    std::vector<double> y(nz, 0.0);
+    std::vector<double> y(nf, 0.0);
     int kept = 0;
-    for (int j = 0; j < nz; ++j) {
+    for (int j = 0; j < nf; ++j) {
         if (!(sig[j] > cut)) continue;
         ++kept;
         double d = 0;
         for (int k = 0; k < p; ++k) d += R[(size_t)j * p + k] * cvec[k];
         d /= sig[j] * sig[j];  // (u_j . c) / sigma_j with u_j = R_j / sigma_j
-        for (int k = 0; k < nz; ++k) y[k] += V[(size_t)j * nz + k] * d;
+        for (int k = 0; k < nf; ++k) y[k] += V[(size_t)j * nf + k] * d;
     }
     std::vector<double> x(nz);
-    for (int j = 0; j < nz; ++j) x[j] = y[j] / cn[j];
+    for (int j = 0; j < nf; ++j) x[j] = y[j] / cn[j];
+    for (int e = 0; e < nc; ++e) {
+        double v = 0.0;
+        for (int f = 0; f < nf; ++f) v += TE[(size_t)e * nf + f] * x[f];
+        x[nf + e] = v;
+    }
 
     // Outputs: K~ (Eq. 1), Khat_l, c_real.
     out->k_tilde.assign(L, 0.0);
@@ -319,7 +384,7 @@ int fit_split_lsq(const double *K, int lmax, int l_cut, double theta_cut,
         const double *pr = &Pj[(size_t)j * L];
         for (int l = 0; l < L; ++l) out->c_real[l] += f * pr[l];
     }
-    out->n_unknowns = nz;
+    out->n_unknowns = nf;
     out->n_kept = kept;
     return KSC_OK;
 }

@@ -30,6 +30,9 @@ KSC_ERR_DEVICE_BOUNDS = -5
 KSC_ERR_SVD = -6
 KSC_ERR_UNSUPPORTED = -7
 MODES = {"lsq": 0, "sharp": 1, "none": 2}
+KSC_CUT_C1 = 0    # default: the real-space kernel's value and slope vanish at theta_cut
+KSC_CUT_C0 = 1    # value only
+KSC_CUT_FREE = 2  # unconstrained fit (K_r may jump at the cut)
 
 # Every symbol include/ksconv.h declares.
 EXPORTS = [
@@ -49,7 +52,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("oversample", ctypes.c_int),
                 ("svd_rcond", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("n_intervals", ctypes.c_int), ("path", ctypes.c_int),
-                ("tensor", ctypes.c_int)]
+                ("tensor", ctypes.c_int), ("cut_continuity", ctypes.c_int)]
 
 
 class Desc(ctypes.Structure):
@@ -162,7 +165,10 @@ def _stream(stream):
 def default_opts(**kw) -> Opts:
     o = Opts()
     _check(_lib.ksc_default_opts(ctypes.byref(o)), "ksc_default_opts")
+    names = {f for f, _ in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown split option {k!r} (known: {sorted(names)})")
         setattr(o, k, MODES[v] if k == "mode" else v)
     return o
 
