@@ -321,6 +321,8 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": workload_desc({"n_pairs_per_map": n_pairs, "n_intervals": info["n_intervals"],
+                                 "split": "weighted least squares (Eq. 3-5), C_l^in = 1/(l+10)^2, "
+                                          "real-space part vanishing with zero slope at theta_cut",
                                  "split_fit_s": round(t_split, 2),
                                  "eq6_frac_error_alpha5": info["frac_error"],
                                  "parallelism": f"independent maps x{world}"}),
@@ -344,14 +346,16 @@ def run_ours(args, world, rank, local):
     sp.close()
 
 
-def run_multimap(K, torch, dev, stream, pk):
-    """64 maps at nside 1024 sharing one split (15' beam, l_max 3071, l_cut 768,
-    theta_cut 480'): the belt ring pairs as a tcgen05 contraction (TF32 x3, FP32
-    accumulate).  Times the tensor stage alone (its roofline) and one whole
-    multi-map call (maps/s)."""
-    nside, lmax, n_maps = 1024, 3071, 64
-    b = inputs.gaussian_beam(lmax, 15.0 * ARC)
-    sp = K.make_split(b, nside, 768, 480.0 * ARC, cl_in=inputs.cl_grf(lmax))
+def run_multimap(K, torch, dev, stream, pk, nside=1024, n_maps=64):
+    """n_maps maps sharing one split (at nside 1024: 15' beam, l_max 3071, l_cut 768,
+    theta_cut 480'; other nside scale every angle by 1024/nside): the belt ring pairs
+    as a tcgen05 contraction (TF32 x3, FP32 accumulate).  Times the tensor stage alone
+    (its roofline) and one whole multi-map call (maps/s)."""
+    sc = 1024.0 / nside
+    lmax, lcut = 3 * nside - 1, (3 * nside) // 4
+    fwhm, tc = 15.0 * sc * ARC, 480.0 * sc * ARC
+    b = inputs.gaussian_beam(lmax, fwhm)
+    sp = K.make_split(b, nside, lcut, tc, cl_in=inputs.cl_grf(lmax))
     n_pairs = K.count_pairs(sp)
     info = K.split_info(sp)
     npix = 12 * nside * nside
@@ -381,8 +385,8 @@ def run_multimap(K, torch, dev, stream, pk):
     useful = 2.0 * belt_pairs * n_maps / t_belt / 1e12
     tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
     sp.close()
-    return {"workload": f"{n_maps} maps x nside {nside}, shared 15' split, l_cut 768, "
-                        "theta_cut 480'",
+    return {"workload": f"{n_maps} maps x nside {nside}, shared {fwhm / ARC:.3g}' split, "
+                        f"l_max {lmax}, l_cut {lcut}, theta_cut {tc / ARC:.4g}'",
             "maps_per_s": n_maps / t_all, "ms_per_call": 1e3 * t_all,
             "pairs_per_map": n_pairs,
             "tensor_stage": {"kernel": "conv_belt_mma_kernel", "ms": 1e3 * t_belt,
@@ -500,11 +504,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multimap", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--multimap-only", action="store_true",
+                    help="only the map-stack (tensor-core) section, at --mm-nside / --mm-maps")
+    ap.add_argument("--mm-nside", type=int, default=1024)
+    ap.add_argument("--mm-maps", type=int, default=64)
     ap.add_argument("--workload", default="nside2048", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
     world, rank, local = dist_setup()
+    if args.multimap_only and args.impl != "reference":
+        import torch
+        from paper_1409_4441_gb300 import ksconv as K
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        print(json.dumps(run_multimap(K, torch, dev, torch.cuda.current_stream(), peaks(),
+                                      nside=args.mm_nside, n_maps=args.mm_maps)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
