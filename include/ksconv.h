@@ -323,6 +323,61 @@ int ksc_device_status(const ksc_split *s, void *stream);
 int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
                             int n_intervals, float *d_table, void *stream);
 
+/* ---- surrogate split selector (learned error / cost model) ------------ */
+/*
+ * A 4-64-64-2 multilayer perceptron (tanh hidden layers, FP32) that predicts,
+ * for a split described by x = (log2 nside, ln FWHM[rad], ln l_cut,
+ * ln theta_cut[rad]), y = (log10 eps_C, log10 t_conv[ms]): the measured
+ * fractional-rms C_l error of the split convolution and the GPU time of its
+ * real-space part.  It stands beside the paper's Eq. 6 error estimate and
+ * Eq. 7-8 cost models (Sec. 2 scan) so a split meeting an error bound can be
+ * chosen without trial runs; a measured run remains the judge.  It is trained
+ * on the GPU by the library's own forward / backward / Adam kernels (the paper
+ * has no counterpart).  Parameters: one flat FP32 array of
+ * ksc_mlp_n_params() values, W1[4][64] b1[64] W2[64][64] b2[64] W3[64][2] b3[2]
+ * (row-major).  Inputs and targets are standardised inside the kernels with
+ * the mean / standard deviation given to ksc_mlp_set_norm (default 0 / 1).
+ * Loss: mean over samples and both outputs of the squared standardised error.
+ */
+typedef struct ksc_mlp ksc_mlp; /* opaque, library-owned */
+
+int ksc_mlp_n_params(void);
+/* New model with Glorot-uniform weights from a splitmix64 stream of `seed`,
+ * zero biases, zero Adam state.  Synchronous.  Errors: ARG, NOMEM, CUDA. */
+int ksc_mlp_create(unsigned long long seed, ksc_mlp **out);
+/* Standardisation constants (host arrays of 4, 4, 2, 2 floats; std > 0). */
+int ksc_mlp_set_norm(ksc_mlp *m, const float *x_mean, const float *x_std,
+                     const float *y_mean, const float *y_std);
+int ksc_mlp_get_params(const ksc_mlp *m, float *h_params);  /* synchronous */
+int ksc_mlp_set_params(ksc_mlp *m, const float *h_params);  /* synchronous */
+/* d_y[n][2] = model(d_x[n][4]) (device arrays, unstandardised units).
+ * Asynchronous on `stream`. */
+int ksc_mlp_predict(const ksc_mlp *m, const float *d_x, int n, float *d_y,
+                    void *stream);
+/* Gradient of the loss over the n samples (d_x[n][4], targets d_t[n][2],
+ * device) with respect to the parameters, into h_grad[ksc_mlp_n_params()]
+ * (host); *h_loss (may be NULL) receives the loss.  Synchronous (legacy
+ * default stream). */
+int ksc_mlp_grad(const ksc_mlp *m, const float *d_x, const float *d_t, int n,
+                 float *h_grad, float *h_loss);
+/* `epochs` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8, step size lr),
+ * one epoch replayed as a CUDA graph on `stream`; *h_loss (may be NULL)
+ * receives the loss evaluated in the last epoch (before its update), after
+ * which the call has synchronised the stream. */
+int ksc_mlp_train(ksc_mlp *m, const float *d_x, const float *d_t, int n,
+                  int epochs, float lr, void *stream, float *h_loss);
+/* Choose among n candidate splits h_x[n][4] (host): predicts on the GPU and
+ * returns in *best the candidate of least cost among those whose predicted
+ * log10 eps_C <= log10_bound - margin, or -1 if none.  The cost of a
+ * candidate is max(predicted GPU time, h_host_ms[i]) -- the two halves of the
+ * split run concurrently (Fig. 1) -- with h_host_ms (may be NULL: GPU time
+ * only) the caller's host cost of its harmonic half in ms (e.g. Eq. 8's
+ * l_cut^2 l_max model on the caller's host).  h_pred (may be NULL) receives
+ * the n x 2 predictions.  Synchronous. */
+int ksc_mlp_select(const ksc_mlp *m, const float *h_x, int n, double log10_bound,
+                   double margin, const double *h_host_ms, int *best, float *h_pred);
+void ksc_mlp_free(ksc_mlp *m);
+
 /* Release a split and its device memory (NULL is a no-op). */
 void ksc_free_split(ksc_split *s);
 

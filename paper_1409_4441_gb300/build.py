@@ -34,18 +34,22 @@ def sources():
                   if f.endswith((".cu", ".cpp")))
 
 
+# Host code is compiled without floating-point contraction so that the split fit
+# gives the same results on x86 and Arm hosts.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3,-ffp-contract=off"]
+STAMP = os.path.join(OBJDIR, "flags.txt")
+
+
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
     deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "ksconv.h"))
+    deps.append(STAMP)
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
-           "-Xcompiler", "-fPIC,-fopenmp,-O3", "-c", src, "-o", obj]
-    if src.endswith(".cu"):
-        cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
-    else:
-        cmd[1:1] = ["-x", "cu"] if False else []
+    cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+    if src.endswith(".cu") and verbose:
+        cmd[1:1] = ["-Xptxas", "-v"]
     out = subprocess.run(cmd, capture_output=True, text=True)
     if out.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{out.stdout}\n{out.stderr}")
@@ -56,6 +60,11 @@ def _compile(src: str, verbose: bool) -> str:
 
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OBJDIR, exist_ok=True)
+    want = " ".join([*ARCH, *FLAGS])
+    have = open(STAMP).read() if os.path.exists(STAMP) else ""
+    if have != want:  # compiler flags changed: every object is stale
+        with open(STAMP, "w") as f:
+            f.write(want)
     if force:
         for f in os.listdir(OBJDIR):
             os.remove(os.path.join(OBJDIR, f))

@@ -73,7 +73,12 @@ void legendre_row(int lmax, double x, double *row) {
 bool jacobi_svd(int p, int n, std::vector<double> &R, std::vector<double> &V) {
     V.assign((size_t)n * n, 0.0);
     for (int j = 0; j < n; ++j) V[(size_t)j * n + j] = 1.0;
-    for (int sweep = 0; sweep < 80; ++sweep) {
+    // columns whose squared norm is below tiny * ||R||_F^2 are numerically null:
+    // rotating them against each other only shuffles rounding noise
+    double fro = 0.0;
+    for (size_t k = 0; k < (size_t)p * n; ++k) fro += R[k] * R[k];
+    const double tiny = 1e-28 * fro;
+    for (int sweep = 0; sweep < 200; ++sweep) {
         bool rotated = false;
         for (int a = 0; a < n - 1; ++a) {
             double *ca = &R[(size_t)a * p];
@@ -86,6 +91,7 @@ bool jacobi_svd(int p, int n, std::vector<double> &R, std::vector<double> &V) {
                     ga += ca[k] * cb[k];
                 }
                 if (ga == 0.0 || std::fabs(ga) <= 1e-15 * std::sqrt(al * be)) continue;
+                if (al < tiny || be < tiny) continue;
                 rotated = true;
                 double zeta = (be - al) / (2.0 * ga);
                 double t = (zeta >= 0 ? 1.0 : -1.0) /

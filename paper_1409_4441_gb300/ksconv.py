@@ -44,6 +44,9 @@ EXPORTS = [
     "ksc_free_split", "ksc_build_table_noalloc",
     "ksc_batch_default_opts", "ksc_batch_create", "ksc_batch_run", "ksc_batch_autotune",
     "ksc_batch_info", "ksc_batch_status", "ksc_batch_free",
+    "ksc_mlp_n_params", "ksc_mlp_create", "ksc_mlp_set_norm", "ksc_mlp_get_params",
+    "ksc_mlp_set_params", "ksc_mlp_predict", "ksc_mlp_grad", "ksc_mlp_train", "ksc_mlp_select",
+    "ksc_mlp_free",
     "ksc_status_string", "ksc_last_error",
 ]
 
@@ -112,6 +115,16 @@ _sig = {
     "ksc_batch_info": [_vp, ctypes.POINTER(BatchDesc)],
     "ksc_batch_status": [_vp, _vp],
     "ksc_batch_free": [_vp],
+    "ksc_mlp_n_params": [],
+    "ksc_mlp_create": [ctypes.c_ulonglong, ctypes.POINTER(_vp)],
+    "ksc_mlp_set_norm": [_vp, _vp, _vp, _vp, _vp],
+    "ksc_mlp_get_params": [_vp, _vp],
+    "ksc_mlp_set_params": [_vp, _vp],
+    "ksc_mlp_predict": [_vp, _vp, _i, _vp, _vp],
+    "ksc_mlp_grad": [_vp, _vp, _vp, _i, _vp, _vp],
+    "ksc_mlp_train": [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp],
+    "ksc_mlp_select": [_vp, _vp, _i, _d, _d, _vp, ctypes.POINTER(_i), _vp],
+    "ksc_mlp_free": [_vp],
     "ksc_status_string": [_i],
     "ksc_last_error": [],
 }
@@ -121,6 +134,7 @@ for _name, _args in _sig.items():
     _f.restype = _i
 _lib.ksc_free_split.restype = None
 _lib.ksc_batch_free.restype = None
+_lib.ksc_mlp_free.restype = None
 _lib.ksc_status_string.restype = ctypes.c_char_p
 _lib.ksc_last_error.restype = ctypes.c_char_p
 
@@ -397,3 +411,114 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _f32_host(a, cols):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != cols:
+        raise ValueError(f"expected an (n, {cols}) array")
+    return a
+
+
+class MLP:
+    """The surrogate split selector (ksc_mlp_*): a 4-64-64-2 network trained and
+    evaluated by the library's CUDA kernels.  Device arrays are float32 CUDA
+    tensors of shape (n, 4) inputs / (n, 2) targets."""
+
+    def __init__(self, seed: int = 0):
+        h = _vp()
+        _check(_lib.ksc_mlp_create(ctypes.c_ulonglong(seed), ctypes.byref(h)), "ksc_mlp_create")
+        self._h = h.value
+
+    @staticmethod
+    def n_params() -> int:
+        return _lib.ksc_mlp_n_params()
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("model already freed")
+        return self._h
+
+    def set_norm(self, x_mean, x_std, y_mean, y_std):
+        a = [np.ascontiguousarray(v, dtype=np.float32) for v in (x_mean, x_std, y_mean, y_std)]
+        _check(_lib.ksc_mlp_set_norm(self.handle, *[v.ctypes.data for v in a]), "ksc_mlp_set_norm")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params(), dtype=np.float32)
+        _check(_lib.ksc_mlp_get_params(self.handle, out.ctypes.data), "ksc_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.n_params():
+            raise ValueError("wrong parameter count")
+        _check(_lib.ksc_mlp_set_params(self.handle, p.ctypes.data), "ksc_mlp_set_params")
+
+    def predict(self, d_x, d_y=None, stream=None):
+        import torch
+        n = d_x.shape[0]
+        if d_y is None:
+            d_y = torch.empty((n, 2), dtype=torch.float32, device=d_x.device)
+        _check(_lib.ksc_mlp_predict(self.handle, _dptr(d_x), n, _dptr(d_y), _stream(stream)),
+               "ksc_mlp_predict")
+        return d_y
+
+    def grad(self, d_x, d_t):
+        g = np.empty(self.n_params(), dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.ksc_mlp_grad(self.handle, _dptr(d_x), _dptr(d_t), d_x.shape[0], g.ctypes.data,
+                                 ctypes.byref(loss)), "ksc_mlp_grad")
+        return g, float(loss.value)
+
+    def train(self, d_x, d_t, epochs: int, lr: float = 1e-3, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(_lib.ksc_mlp_train(self.handle, _dptr(d_x), _dptr(d_t), d_x.shape[0], int(epochs),
+                                  ctypes.c_float(lr), _stream(stream), ctypes.byref(loss)),
+               "ksc_mlp_train")
+        return float(loss.value)
+
+    def select(self, h_x, log10_bound: float, margin: float = 0.0, host_ms=None):
+        """Index of the least-cost candidate whose predicted log10 eps_C clears the
+        bound by `margin` decades (-1 if none), cost = max(predicted GPU ms,
+        host_ms[i]) (host_ms None: GPU time only); and the (n, 2) predictions."""
+        x = _f32_host(h_x, 4)
+        pred = np.empty((x.shape[0], 2), dtype=np.float32)
+        best = ctypes.c_int()
+        hp = None
+        if host_ms is not None:
+            hm = np.ascontiguousarray(host_ms, dtype=np.float64)
+            if hm.size != x.shape[0]:
+                raise ValueError("host_ms needs one value per candidate")
+            hp = hm.ctypes.data
+        _check(_lib.ksc_mlp_select(self.handle, x.ctypes.data, x.shape[0], float(log10_bound),
+                                   float(margin), hp, ctypes.byref(best), pred.ctypes.data),
+               "ksc_mlp_select")
+        return int(best.value), pred
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ksc_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def harmonic_cost_eq8_ms(l_cut, l_max, cores: int = 1):
+    """Eq. 8's host cost of the harmonic half, 160 s l_cut^2 l_max / 4096^3 (the paper's
+    single 2.8 GHz Core2 core running libpsht), spread over `cores` cores, in ms."""
+    return 160e3 * np.asarray(l_cut, float) ** 2 * np.asarray(l_max, float) / 4096.0 ** 3 / cores
+
+
+def split_features(nside, fwhm_rad, l_cut, theta_cut_rad) -> np.ndarray:
+    """Surrogate inputs (log2 nside, ln FWHM, ln l_cut, ln theta_cut), float32 (n, 4)."""
+    nside, fwhm, lc, tc = (np.atleast_1d(np.asarray(v, dtype=np.float64))
+                           for v in (nside, fwhm_rad, l_cut, theta_cut_rad))
+    return np.stack([np.log2(nside), np.log(fwhm), np.log(lc), np.log(tc)], axis=1).astype(np.float32)
