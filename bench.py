@@ -346,16 +346,36 @@ def run_ours(args, world, rank, local):
     sp.close()
 
 
+def _event_ms(fn, stream, torch, reps=3):
+    """Mean CUDA-event time (ms) of fn() on `stream` after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(reps):
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        fn()
+        b_.record(stream)
+        ev.append((a_, b_))
+    torch.cuda.synchronize()
+    return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
+
+
 def run_multimap(K, torch, dev, stream, pk, nside=1024, n_maps=64):
     """n_maps maps sharing one split (at nside 1024: 15' beam, l_max 3071, l_cut 768,
-    theta_cut 480'; other nside scale every angle by 1024/nside): the belt ring pairs
-    as a tcgen05 contraction (TF32 x3, FP32 accumulate).  Times the tensor stage alone
-    (its roofline) and one whole multi-map call (maps/s)."""
+    theta_cut 480'; other nside scale every angle by 1024/nside).  Default path: the
+    cap ring pairs as a tcgen05 contraction (each weight shared by 16 images x 8 maps,
+    TF32 x3, FP32 accumulate), the belt ring pairs on the FFMA circulant kernel.
+    Reports maps/s of the whole call against the per-map FFMA path, the roofline of
+    the tensor cap stage, and the tensor form of the belt stage for comparison."""
     sc = 1024.0 / nside
     lmax, lcut = 3 * nside - 1, (3 * nside) // 4
     fwhm, tc = 15.0 * sc * ARC, 480.0 * sc * ARC
     b = inputs.gaussian_beam(lmax, fwhm)
-    sp = K.make_split(b, nside, lcut, tc, cl_in=inputs.cl_grf(lmax))
+    cl = inputs.cl_grf(lmax)
+    sp = K.make_split(b, nside, lcut, tc, cl_in=cl)                 # tensor caps (default)
+    sf = K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=1)       # FFMA only
+    sb = K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=2)       # tensor belt as well
     n_pairs = K.count_pairs(sp)
     info = K.split_info(sp)
     npix = 12 * nside * nside
@@ -363,38 +383,37 @@ def run_multimap(K, torch, dev, stream, pk, nside=1024, n_maps=64):
     for i in range(n_maps):
         x[i] = torch.from_numpy(inputs.white_noise_map(nside, inputs.seed_for(4, i)).astype(np.float32))
     y = torch.empty_like(x)
-    K.conv_real_multimap_stage(sp, x, y, n_maps, 1)
-    torch.cuda.synchronize()
-    ev = []
-    for _ in range(3):
-        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        K.conv_real_multimap_stage(sp, x, y, n_maps, 1)
-        b_.record(stream)
-        ev.append((a_, b_))
-    torch.cuda.synchronize()
-    t_belt = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev) / 1e3
-    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a_.record(stream)
-    K.conv_real_multimap(sp, x, y, n_maps)
-    b_.record(stream)
-    torch.cuda.synchronize()
-    t_all = a_.elapsed_time(b_) / 1e3
-    K.device_status(sp)
+    t_all = _event_ms(lambda: K.conv_real_multimap(sp, x, y, n_maps), stream, torch, reps=2) / 1e3
+    t_belt = _event_ms(lambda: K.conv_real_multimap_stage(sp, x, y, n_maps, 1), stream, torch) / 1e3
+    t_caps = _event_ms(lambda: K.conv_real_multimap_stage(sp, x, y, n_maps, 2), stream, torch) / 1e3
+    t_ffma = _event_ms(lambda: K.conv_real_multimap(sf, x, y, n_maps), stream, torch, reps=1) / 1e3
+    t_tbelt = _event_ms(lambda: K.conv_real_multimap_stage(sb, x, y, n_maps, 1), stream, torch,
+                        reps=2) / 1e3
+    for s_ in (sp, sf, sb):
+        K.device_status(s_)
     belt_pairs = info["n_pairs_belt"]
-    useful = 2.0 * belt_pairs * n_maps / t_belt / 1e12
+    cap_pairs = n_pairs - belt_pairs
     tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
-    sp.close()
+    caps_tf = 2.0 * cap_pairs * n_maps / t_caps / 1e12
+    tbelt_tf = 2.0 * belt_pairs * n_maps / t_tbelt / 1e12
+    for s_ in (sp, sf, sb):
+        s_.close()
     return {"workload": f"{n_maps} maps x nside {nside}, shared {fwhm / ARC:.3g}' split, "
                         f"l_max {lmax}, l_cut {lcut}, theta_cut {tc / ARC:.4g}'",
             "maps_per_s": n_maps / t_all, "ms_per_call": 1e3 * t_all,
-            "pairs_per_map": n_pairs,
-            "tensor_stage": {"kernel": "conv_belt_mma_kernel", "ms": 1e3 * t_belt,
-                             "achieved": useful, "unit": "TFLOP/s",
-                             "peak": tf32_peak, "frac": useful / tf32_peak,
-                             "note": "2 FLOP per belt-belt pixel pair per map; peak = measured "
-                                     "bf16 burst x (1.1/2.25) nominal TF32 ratio; the kernel "
-                                     "issues 3 TF32 MMAs per product for FP32 accuracy"}}
+            "maps_per_s_ffma": n_maps / t_ffma, "ms_per_call_ffma": 1e3 * t_ffma,
+            "pairs_per_map": n_pairs, "belt_pairs_per_map": belt_pairs,
+            "stages_ms": {"belt_ffma": 1e3 * t_belt, "caps_tensor": 1e3 * t_caps},
+            "tensor_stage": {"kernel": "conv_sym_mma_kernel", "ms": 1e3 * t_caps,
+                             "achieved": caps_tf, "unit": "TFLOP/s", "peak": tf32_peak,
+                             "frac": caps_tf / tf32_peak,
+                             "note": "2 FLOP per cap pixel pair per map; peak = measured bf16 "
+                                     "burst x (1.1/2.25) nominal TF32 ratio; 3 TF32 MMAs per "
+                                     "product for FP32 accuracy"},
+            "belt_tensor_form": {"kernel": "conv_belt_mma_kernel", "ms": 1e3 * t_tbelt,
+                                 "achieved": tbelt_tf, "unit": "TFLOP/s",
+                                 "frac": tbelt_tf / tf32_peak,
+                                 "note": "opts.tensor = 2; slower than the FFMA belt stage"}}
 
 
 def _time_calls(fn, stream, torch, reps=3):

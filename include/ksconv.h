@@ -73,9 +73,13 @@ typedef struct {
                           wavelength, at most 8192)                             */
     int path;          /* 0 (default): circulant belt kernel + symmetric gather;
                           1: general ring-pair gather only (reference path)   */
-    int tensor;        /* 0 (default): ksc_conv_real_multimap runs belt ring
-                          pairs on the tcgen05 tensor cores (TF32 x3, FP32
-                          accumulate) when n_maps >= 16; 1: FFMA kernels only */
+    int tensor;        /* map stacks (ksc_conv_real_multimap, n_maps >= 16):
+                          0 (default): the symmetric (cap) ring pairs on the
+                          tcgen05 tensor cores (TF32 x3, FP32 accumulate),
+                          the belt ring pairs on the FFMA circulant kernel;
+                          1: FFMA kernels only; 2: both kinds of ring pair on
+                          the tensor cores (the belt's tensor form is slower
+                          than its circulant FFMA form on GB300)            */
     int cut_continuity; /* LSQ mode: how the fitted real-space kernel meets the
                           cut (the truncation "to a limit theta_cut" of Sec. 2):
                           KSC_CUT_C1 (0, default) value and slope vanish at
@@ -166,10 +170,13 @@ int ksc_conv_real_rings(const ksc_split *s, const float *d_in, float *d_out,
 
 /*
  * n_maps maps sharing one split: d_in and d_out are [n_maps][12 nside^2]
- * device arrays (map-major).  Asynchronous.  With n_maps >= 16 the belt ring
- * pairs run on the tensor cores through a per-split workspace (the map stack
- * pre-split into TF32 tiles, about 2.6x the input size), allocated on the
- * first such call and reused; multi-map calls on one split must therefore not
+ * device arrays (map-major).  Asynchronous.  With n_maps >= 16 the cap ring
+ * pairs run on the tensor cores (each kernel weight evaluated once for a
+ * group of 8 maps and their 16 symmetry images; results equal the per-map
+ * path to about 2e-6 of the rms).  With opts.tensor = 2 the belt ring pairs
+ * also run on the tensor cores, through a per-split workspace (the map stack
+ * pre-split into TF32 tiles, about 2.6x the input size) allocated on the
+ * first such call and reused; multi-map calls on such a split must not
  * overlap on the GPU.
  */
 int ksc_conv_real_multimap(const ksc_split *s, const float *d_in,
@@ -284,7 +291,7 @@ int ksc_conv_real_stage(const ksc_split *s, const float *d_in, float *d_out,
                         int stage, void *stream);
 
 /* The same two stages for a stack of n_maps maps ([n_maps][Npix] device
- * arrays); stage 1 uses the tensor kernel under the same rule as
+ * arrays); each stage uses the tensor kernel under the same rule as
  * ksc_conv_real_multimap.  Stage 1 then stage 2 equals that call bit for bit. */
 int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in,
                                  float *d_out, int n_maps, int stage,

@@ -140,7 +140,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     s->tensor = o.tensor;
     s->mma_ext0 = ((w_ext + 32) + 31) & ~31;
     s->mma_ntiles = (s->mma_ext0 + 4 * nside + (((w_ext + 160) + 31) & ~31)) / 32;
-    if (ksc::belt_mma_smem(s->w_cap) > 220u * 1024) s->tensor = 1;
+    // the belt tensor kernel needs its weight window in shared memory
+    if (s->tensor == 2 && ksc::belt_mma_smem(s->w_cap) > 220u * 1024) s->tensor = 0;
     s->ring_first_item[nr] = (int)items.size();
     s->ring_first_sym[nr] = (int)items_sym.size();
     s->ring_first_belt[nr] = (int)items_belt.size();
@@ -304,7 +305,7 @@ ksc_split_opts resolve_opts(const ksc_split_opts *opts) {
         if (!(o.svd_rcond > 0.0)) o.svd_rcond = 1e-6;
         if (!(o.alpha > 0.0)) o.alpha = 5.0;
         if (o.path != 1) o.path = 0;
-        if (o.tensor != 1) o.tensor = 0;
+        if (o.tensor != 1 && o.tensor != 2) o.tensor = 0;
         if (o.cut_continuity < KSC_CUT_C1 || o.cut_continuity > KSC_CUT_FREE)
             o.cut_continuity = KSC_CUT_C1;
     }
@@ -357,7 +358,8 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
         return KSC_OK;
     }
     const bool whole = r0 == 0 && r1 == s->plan.nrings - 1;
-    if (whole && n_maps >= 16 && s->tensor == 0 && s->n_items_mma > 0) {
+    const bool stack = whole && n_maps >= 16;
+    if (stack && s->tensor == 2 && s->n_items_mma > 0) {
         int rc = launch_belt_tensor(s, d_in, d_out, n_maps, stride, st);
         if (rc) return rc;
     } else {
@@ -374,8 +376,12 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
     if (m0 <= m1) { lo = std::min(lo, m0); hi = std::max(hi, m1); }  // mirror in band
     if (lo <= hi) {
         const int c = s->ring_first_sym[lo], d = s->ring_first_sym[hi + 1];
-        e = ksc::launch_conv_sym(s->plan, s->d_items_sym + c, d - c, d_in, d_out, n_maps, stride,
-                                 s->n_items_belt > 0 ? 1 : 0, r0, r1, st);
+        if (stack && s->tensor != 1)
+            e = ksc::launch_conv_sym_mma(s->plan, s->d_items_sym + c, d - c, d_in, d_out, n_maps,
+                                         stride, s->n_items_belt > 0 ? 1 : 0, s->d_err, st);
+        else
+            e = ksc::launch_conv_sym(s->plan, s->d_items_sym + c, d - c, d_in, d_out, n_maps,
+                                     stride, s->n_items_belt > 0 ? 1 : 0, r0, r1, st);
         if (e != cudaSuccess) return cuda_fail(e, "symmetric kernel launch");
     }
     return KSC_OK;
@@ -626,7 +632,7 @@ int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in, float *d
     cudaError_t e;
     if (stage == 1) {
         if (s->path == 1) return KSC_OK;
-        if (n_maps >= 16 && s->tensor == 0 && s->n_items_mma > 0)
+        if (n_maps >= 16 && s->tensor == 2 && s->n_items_mma > 0)
             return launch_belt_tensor(s, d_in, d_out, n_maps, stride, st);
         else
             e = ksc::launch_conv_belt(s->plan, s->d_items_belt, s->n_items_belt, s->seg_cap,
@@ -635,6 +641,10 @@ int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in, float *d
         if (s->path == 1)
             e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, n_maps,
                                          stride, 0, nullptr, st);
+        else if (n_maps >= 16 && s->tensor != 1)
+            e = ksc::launch_conv_sym_mma(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out,
+                                         n_maps, stride, s->n_items_belt > 0 ? 1 : 0, s->d_err,
+                                         st);
         else
             e = ksc::launch_conv_sym(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out,
                                      n_maps, stride, s->n_items_belt > 0 ? 1 : 0, 0,

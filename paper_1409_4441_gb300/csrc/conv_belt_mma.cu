@@ -28,6 +28,7 @@
 
 #include "ksc_device.cuh"
 #include "ksc_internal.h"
+#include "ksc_tc.cuh"
 
 namespace ksc {
 namespace {
@@ -36,7 +37,6 @@ constexpr int kM = 128;             // outputs per block (TMEM lanes)
 constexpr int kN = 64;              // maps per group (TMEM columns)
 constexpr int kKT = 32;             // positions per K tile (4 MMAs of K = 8)
 constexpr int kThreads = 128;
-constexpr int kMaxWait = 1 << 22;
 constexpr int kTotStride = kN + 1;  // padded rows: conflict-free per-row access
 constexpr int kTileB = kN * kKT;    // floats per B tile part (hi or lo)
 
@@ -46,63 +46,15 @@ struct Stage {  // one operand stage, canonical no-swizzle K-major tiles
     float b[2 * kTileB];  // hi then lo, copied as one block
 };
 
-__device__ __forceinline__ uint32_t saddr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+using tc::mbar_wait;
+using tc::mma_commit;
+using tc::mma_tf32;
+using tc::saddr;
+using tc::split_tf32;
 
-// element (row, k) of a K-major tile with kKT columns: 8-row x 16-byte core
-// matrices, K-adjacent core matrices 128 B apart, 8-row groups kKT*32 B apart
-__host__ __device__ __forceinline__ int toff(int row, int k) {
-    return (row >> 3) * (kKT * 8) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
-}
+__host__ __device__ __forceinline__ int toff(int row, int k) { return tc::toff<kKT>(row, k); }
 
-__device__ __forceinline__ uint64_t smem_desc(const void *p) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr(p) & 0x3FFFF) >> 4);
-    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;        // leading (K) core-matrix stride
-    d |= (uint64_t)(((kKT * 32u) >> 4) & 0x3FFF) << 32;  // stride (8-row group) offset
-    d |= (uint64_t)1 << 46;                              // descriptor version
-    return d;                                            // no swizzle, base offset 0
-}
-
-__device__ __forceinline__ void split_tf32(float x, float *hi, float *lo) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    const float hf = __uint_as_float(h);
-    uint32_t l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hf));
-    *hi = hf;
-    *lo = __uint_as_float(l);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < kMaxWait; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(saddr(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
-                                         uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            saddr(bar))
-        : "memory");
-}
+__device__ __forceinline__ uint64_t smem_desc(const void *p) { return tc::smem_desc<kKT>(p); }
 
 // B tiles: for belt ring index qi, tile u (positions 32u - ext0 .. +31),
 // map group g: kN x kKT hi floats then kN x kKT lo floats.
@@ -177,8 +129,7 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                           ((uint32_t)(kM >> 4) << 24);  // F32 += TF32 x TF32, K-major
+    const uint32_t idesc = tc::idesc_tf32(kM, kN);  // F32 += TF32 x TF32, K-major
     uint32_t ph_full[2] = {0u, 0u}, ph_done[2] = {0u, 0u};
     int pending[2] = {0, 0};
     int copy_b = -1;  // stage of the last bulk copy thread 0 issued and has not waited for

@@ -33,6 +33,7 @@
 // on an SM to hide the latency of the double-float chains.
 #include "ksc_device.cuh"
 #include "ksc_internal.h"
+#include "ksc_sym.cuh"
 
 namespace ksc {
 namespace {
@@ -51,39 +52,6 @@ template <int T_, int LANES_, int SPAN_, int MINB_> struct SymShape {
 using ShapeFull = SymShape<128, 1, 512, 3>;   // variant 0
 using ShapeHalf = SymShape<64, 1, 256, 6>;    // variant 1
 using ShapePair = SymShape<128, 2, 384, 5>;   // variant 2
-
-struct SymRing {  // one (output ring, input ring) pair
-    DF A, B, c;
-    float hw;
-    int len, start, start_m, phase, small;
-};
-
-__device__ __forceinline__ int pmod(int a, int n) {
-    int r = a % n;
-    return r < 0 ? r + n : r;
-}
-
-// Window [klo, khi] of input positions for output class k (one pixel of margin
-// around |dphi| <= dphi_max; the whole ring, once, when a partial window could
-// reach the ring's length).  The choice depends on the ring pair only, so both
-// ends are nondecreasing in k and the CTA's union of windows runs from the
-// first class's klo to the last class's khi.
-__device__ __forceinline__ void window(int k, int t, int L, const SymRing &g, long long *num,
-                                       int *klo, int *khi) {
-    const int L2 = g.len;
-    *num = (long long)(2 * k + t) * L2 - (long long)g.phase * L;
-    const float kc = (float)*num / (float)(2 * L);
-    int lo, hi;
-    if (2.0f * g.hw + 3.0f >= (float)L2) {
-        lo = (int)floorf(kc) - L2 / 2;
-        hi = lo + L2 - 1;
-    } else {
-        lo = (int)floorf(kc - g.hw);
-        hi = (int)ceilf(kc + g.hw);  // hi - lo + 1 <= 2 hw + 3 < L2
-    }
-    *klo = lo;
-    *khi = hi;
-}
 
 __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
     const float y = v - *comp;
@@ -114,16 +82,7 @@ __device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing 
 #pragma unroll
     for (int ee = 0; ee < NE; ++ee) {
         const int e = S::LANES == 2 ? 2 * h + ee : ee;
-        const float Nf = N0 - (float)e * step;
-        const float xh = Nf * g.c.h;
-        const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
-        const DF sn = SMALL ? sin_df_small(xh, xl) : sin_df(xh, xl);
-        const int kp = kq + e;
-        int ti;
-        float f;
-        const bool in = chord_to_table_sel(g.A, g.B, sn, P.nint2, &ti, &f);
-        const float wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
-        w[ee] = (in && kp >= a && kp <= b) ? wv : 0.0f;
+        w[ee] = sym_weight<SMALL>(P, g, N0 - (float)e * step, kq + e, a, b);
     }
     if constexpr (S::LANES == 2) {  // swap halves with the partner lane
         const float o0 = __shfl_xor_sync(pair_mask, w[0], 1);
@@ -209,24 +168,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
     for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
         const int nq = min(kRingChunk, rg.y - q0 + 1);
         __syncthreads();
-        if (tid < nq) {
-            const int q = q0 + tid;
-            const DevRing Qr = P.d_rings[q];
-            const PairInfo pi = P.d_pairs[P.d_pair_base[r] + (q - rg.x)];
-            SymRing g;
-            g.A = DF{pi.Ah, pi.Al};
-            g.B = DF{pi.Bh, pi.Bl};
-            g.c = DF{pi.ch, pi.cl};
-            g.hw = (skip_belt_inputs && q >= P.belt_lo && q <= P.belt_hi) ? -1.0f : pi.hw;
-            g.len = Qr.len;
-            g.start = Qr.start;
-            g.start_m = P.d_rings[P.nrings - 1 - q].start;
-            g.phase = Qr.phase;
-            // |dphi / 2| < 0.25 over the whole (partial) window: the cheap sine
-            g.small = (2.0f * pi.hw + 3.0f < (float)Qr.len) &&
-                      ((pi.hw + 1.0f) * 3.14159265f / (float)Qr.len < 0.25f);
-            sR[tid] = g;
-        }
+        if (tid < nq) sR[tid] = load_sym_ring(P, r, q0 + tid, rg, skip_belt_inputs);
         __syncthreads();
         for (int qi = 0; qi < nq; ++qi) {
             const SymRing g = sR[qi];
@@ -234,17 +176,17 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             const int L2 = g.len, Q2 = L2 / 4;
             long long num, numx;
             int klo, khi, U0, U1, dummy;
-            window(k, t, L, g, &num, &klo, &khi);
-            window(k_first, t, L, g, &numx, &U0, &dummy);
-            window(k_last, t, L, g, &numx, &dummy, &U1);
+            sym_window(k, t, L, g, &num, &klo, &khi);
+            sym_window(k_first, t, L, g, &numx, &U0, &dummy);
+            sym_window(k_last, t, L, g, &numx, &dummy, &U1);
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 // positions this segment needs (the union ends at U1)
                 const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
                 __syncthreads();  // the previous segment is consumed
                 for (int j = tid; j < span; j += T) {
                     const int kp = s0 + j;
-                    const int idx = pmod(kp, L2);
-                    const int idr = pmod(Q2 - kp - g.phase, L2);
+                    const int idx = sym_pmod(kp, L2);
+                    const int idr = sym_pmod(Q2 - kp - g.phase, L2);
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
                         int ia = idx + qq * Q2;

@@ -162,6 +162,15 @@ cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
                                   const BatchEntry *d_entries, const int4 *d_items, int n_items,
                                   int per_sm_cap, int *d_counter, cudaStream_t st);
 
+// tcgen05 gather for map stacks (symmetric ring pairs): items are the
+// symmetric work items (sym_chunk() classes each); maps in groups of
+// sym_mma_maps(); same outputs as launch_conv_sym over the whole map.
+int sym_mma_maps();
+cudaError_t launch_conv_sym_mma(const ConvPlan &p, const WorkItem *d_items, int n_items,
+                                const float *d_in, float *d_out, int n_maps,
+                                long long map_stride, int belt_split, int *d_err,
+                                cudaStream_t st);
+
 // Record the message returned by ksc_last_error() on this thread.
 void set_last_error(const std::string &msg);
 
@@ -202,7 +211,7 @@ struct ksc_split {
     int2 *d_items_mma = nullptr;           // 128-output belt blocks for the tensor kernel
     int n_items_mma = 0;
     int w_cap = 0;                         // widest belt weight window
-    int tensor = 0;                        // 0: tensor kernel for >= 16 maps, 1: never
+    int tensor = 0;                        // ksc_split_opts.tensor (0, 1, 2)
     int mma_ext0 = 0, mma_ntiles = 0;      // ring extension and K tiles per belt ring
     float *d_ws = nullptr;                 // pre-tiled map stack (tensor path workspace)
     size_t ws_floats = 0;

@@ -1,0 +1,88 @@
+// Ring-pair geometry and kernel weights of the symmetric (cap) gather, shared
+// by the FFMA kernel (conv_sym.cu) and the tensor-core kernel for map stacks
+// (conv_sym_mma.cu).
+//
+// For output ring r (L pixels, phase flag t) and input ring q (L' pixels,
+// phase t'), pixel k of r and pixel k' of q are dphi apart with
+// dphi / 2 = N pi / (2 L L'), N = (2k + t) L' - (2k' + t') L an exact
+// integer; the chord in table-position units is u^2 = A + B sin^2(dphi / 2)
+// with the ring-pair constants A, B of the split (double-float, ksc_device.cuh).
+#pragma once
+
+#include "ksc_device.cuh"
+#include "ksc_internal.h"
+
+namespace ksc {
+
+struct SymRing {  // one (output ring, input ring) pair
+    DF A, B, c;
+    float hw;     // half window in input pixels; < 0: no pixel within the cut
+    int len, start, start_m, phase, small;
+};
+
+__device__ __forceinline__ int sym_pmod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// Constants of (output ring r, input ring q); the pair is skipped (hw < 0) when
+// skip_belt_inputs is set and q is a belt ring (the belt kernel covered it).
+__device__ __forceinline__ SymRing load_sym_ring(const ConvPlan &P, int r, int q, int2 rg,
+                                                 bool skip_belt_inputs) {
+    const DevRing Qr = P.d_rings[q];
+    const PairInfo pi = P.d_pairs[P.d_pair_base[r] + (q - rg.x)];
+    SymRing g;
+    g.A = DF{pi.Ah, pi.Al};
+    g.B = DF{pi.Bh, pi.Bl};
+    g.c = DF{pi.ch, pi.cl};
+    g.hw = (skip_belt_inputs && q >= P.belt_lo && q <= P.belt_hi) ? -1.0f : pi.hw;
+    g.len = Qr.len;
+    g.start = Qr.start;
+    g.start_m = P.d_rings[P.nrings - 1 - q].start;
+    g.phase = Qr.phase;
+    // |dphi / 2| < 0.25 over the whole (partial) window: the cheap sine
+    g.small = (2.0f * pi.hw + 3.0f < (float)Qr.len) &&
+              ((pi.hw + 1.0f) * 3.14159265f / (float)Qr.len < 0.25f);
+    return g;
+}
+
+// Window [klo, khi] of input positions for output class k (one pixel of margin
+// around |dphi| <= dphi_max; the whole ring, once, when a partial window could
+// reach the ring's length).  The choice depends on the ring pair only, so both
+// ends are nondecreasing in k and a CTA's union of windows runs from its first
+// class's klo to its last class's khi.
+__device__ __forceinline__ void sym_window(int k, int t, int L, const SymRing &g, long long *num,
+                                           int *klo, int *khi) {
+    const int L2 = g.len;
+    *num = (long long)(2 * k + t) * L2 - (long long)g.phase * L;
+    const float kc = (float)*num / (float)(2 * L);
+    int lo, hi;
+    if (2.0f * g.hw + 3.0f >= (float)L2) {
+        lo = (int)floorf(kc) - L2 / 2;
+        hi = lo + L2 - 1;
+    } else {
+        lo = (int)floorf(kc - g.hw);
+        hi = (int)ceilf(kc + g.hw);  // hi - lo + 1 <= 2 hw + 3 < L2
+    }
+    *klo = lo;
+    *khi = hi;
+}
+
+// Kernel weight of input position kp for the class whose exact integer at
+// position 0 is num (Nf = num - 2 kp L as a float, exact below 2^24); zero
+// outside [a, b] and beyond the cut.  Branch-free, so several evaluations
+// interleave.
+template <bool SMALL>
+__device__ __forceinline__ float sym_weight(const ConvPlan &P, const SymRing &g, float Nf, int kp,
+                                            int a, int b) {
+    const float xh = Nf * g.c.h;
+    const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
+    const DF sn = SMALL ? sin_df_small(xh, xl) : sin_df(xh, xl);
+    int ti;
+    float f;
+    const bool in = chord_to_table_sel(g.A, g.B, sn, P.nint2, &ti, &f);
+    const float wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
+    return (in && kp >= a && kp <= b) ? wv : 0.0f;
+}
+
+} // namespace ksc
