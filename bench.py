@@ -42,6 +42,9 @@ METRIC = "pixel-pair interactions/s and maps/s at nside=2048 vs roofline, at 1e-
 UNIT = "pairs/s"
 N_SM = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
+# capture of the current kernel (profiles/conv_sym_nside2048_dram.md)
+DRAM_TRAFFIC = {"conv_sym_kernel": 117.99e6 + 51.58e6}
 
 
 def workload_desc(extra=None):
@@ -329,7 +332,10 @@ def run_ours(args, world, rank, local):
         "maps_per_s": world * args.steps / elapsed,
         "roofline": {"bound": "alu", "kernel": dom,
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops,
+                     "traffic": DRAM_TRAFFIC.get(dom) if args.workload == "nside2048" else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + "
+                                     "dram__bytes_write.sum, profiles/conv_sym_nside2048_dram.md)",
                      "note": "2 FLOP (one FMA) per in-disc pixel pair the kernel handles; "
                              "peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock"},
         "stages": stages,
