@@ -312,8 +312,10 @@ def run_ours(args, world, rank, local):
                    "sample": f"failed: {e}"}
 
     multimap = None
+    stack = None
     if world == 1 and not args.no_multimap and args.workload == "nside2048":
         multimap = run_multimap(K, torch, dev, stream, pk)
+        stack = run_stack(K, torch, dev, stream, sp, n_pairs, 16, world * args.steps / elapsed)
     batch = None
     if world == 1 and not args.no_batch and args.workload == "nside2048":
         batch = run_batch(K, torch, dev, stream, big_split=sp)
@@ -346,6 +348,7 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "multimap": multimap,
+        "stack_nside2048": stack,
         "batch": batch,
     }
     print(json.dumps(line), flush=True)
@@ -365,6 +368,26 @@ def _event_ms(fn, stream, torch, reps=3):
         ev.append((a_, b_))
     torch.cuda.synchronize()
     return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
+
+
+def run_stack(K, torch, dev, stream, sp, n_pairs, n_maps, single_maps_per_s):
+    """n_maps maps of the benchmark workload itself (nside 2048, the same split) as one
+    map-stack call (cap ring pairs on the tensor cores, belt on the FFMA kernel): maps/s
+    against the single-map path.  Maps: i.i.d. N(0,1) drawn on the device from a seeded
+    generator (throughput does not depend on the values)."""
+    npix = 12 * 2048 * 2048
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(inputs.seed_for(3, 1000))
+    x = torch.randn((n_maps, npix), generator=gen, device=dev, dtype=torch.float32)
+    y = torch.empty_like(x)
+    ms = _event_ms(lambda: K.conv_real_multimap(sp, x, y, n_maps), stream, torch, reps=2)
+    K.device_status(sp)
+    del x, y
+    return {"workload": f"{n_maps} maps x nside 2048, the benchmark split (5' beam, l_cut 1024, "
+                        "theta_cut 240'), one map-stack call",
+            "maps_per_s": n_maps / (ms / 1e3), "ms_per_call": ms,
+            "pairs_per_s": n_maps * n_pairs / (ms / 1e3),
+            "single_map_maps_per_s": single_maps_per_s}
 
 
 def run_multimap(K, torch, dev, stream, pk, nside=1024, n_maps=64):

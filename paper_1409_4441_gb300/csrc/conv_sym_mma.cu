@@ -15,7 +15,7 @@
 // TF32 x3 (hi*hi + hi*lo + lo*hi, FP32 products to about 2^-22) with FP32
 // accumulation in tensor memory; after each ring pair the partial accumulator
 // is Kahan-folded into running sums kept in tensor memory too (columns
-// [0, 128) partial, [128, 256) sum, [256, 384) compensation).  Two threads per
+// [0, 128) partial, [128, 256) sum, [256, 384) compensation).  Four threads per
 // class row build the operand tiles (the weight evaluation is the cost), the
 // operand stages are double-buffered so one tile's MMAs overlap the next
 // tile's build, and every mbarrier wait is bounded: on a timeout the kernel
@@ -35,7 +35,8 @@ constexpr int kImg = 16;          // symmetry images
 constexpr int kMaps = 8;          // maps per group
 constexpr int kN = kImg * kMaps;  // accumulator columns, n = image * kMaps + map
 constexpr int kKT = 32;           // positions per K tile (4 MMAs of K = 8)
-constexpr int kThreads = 256;     // two threads per class row
+constexpr int kThreads = 512;     // four threads per class row
+constexpr int kParts = kThreads / kM;
 constexpr int kRingChunk = 32;
 constexpr uint32_t kColSum = kN, kColCmp = 2 * kN, kTmemCols = 512;
 
@@ -54,20 +55,19 @@ __device__ __forceinline__ void store_split4(float *hi, float *lo, int off, floa
     *reinterpret_cast<float4 *>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
 }
 
-// A tile row `row`, quads half, half + 2, half + 4, half + 6 of the tile
-// (positions pbase + 4 qd .. + 3): weights of class k (integer num, window
-// [a, b]).  The two threads of a row interleave quads so both see the same
-// share of the class's window; quads wholly outside the window are zero
-// without evaluation (the tiles span the union of 128 classes' windows, whose
-// ends shift by about one position per class, so the branch is uniform across
-// a warp except near the window ends).
+// A tile row `row`, quads part, part + 4 of the tile (positions pbase + 4 qd ..
+// + 3): weights of class k (integer num, window [a, b]).  The four threads of
+// a row interleave quads so all see the same share of the class's window;
+// quads wholly outside the window are zero without evaluation (the tiles span
+// the union of 128 classes' windows, whose ends shift by about one position
+// per class, so the branch is uniform across a warp except near the ends).
 template <bool SMALL>
 __device__ __forceinline__ void build_a(const ConvPlan &P, const SymRing &g, Stage &S, int row,
-                                        int half, int pbase, long long num, int L, int a, int b) {
+                                        int part, int pbase, long long num, int L, int a, int b) {
     const float step = (float)(2 * L);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int qd = half + 2 * j;
+    for (int j = 0; j < (kKT / 4) / kParts; ++j) {
+        const int qd = part + kParts * j;
         const int kq = pbase + 4 * qd;
         const int o = tc::toff<kKT>(row, 4 * qd);
         if (kq + 3 < a || kq > b) {
@@ -85,24 +85,22 @@ __device__ __forceinline__ void build_a(const ConvPlan &P, const SymRing &g, Sta
     }
 }
 
-// This lane's 16 B-tile values of the tile starting at pbase (see the
-// assignment in the kernel).
-__device__ __forceinline__ void load_b(const float *const *src, const int *qoff, const bool *live,
+// This lane's 8 B-tile values (two rows, four positions) of the tile starting
+// at pbase (see the assignment in the kernel).
+__device__ __forceinline__ void load_b(const float *const *src, int qoff, const bool *live,
                                        bool reflected, int pbase, int pg, int L2, int Q2, int phase,
                                        float *v) {
     const int pp = pbase + 4 * pg;
     const int base = reflected ? sym_pmod(Q2 - pp - phase, L2) : sym_pmod(pp, L2);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int e = 0; e < 4; ++e) {
+        int ix = reflected ? base - e : base + e;
+        ix += ix < 0 ? L2 : 0;
+        ix -= ix >= L2 ? L2 : 0;
+        ix += qoff;
+        ix -= ix >= L2 ? L2 : 0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int ix = reflected ? base - e : base + e;
-            ix += ix < 0 ? L2 : 0;
-            ix -= ix >= L2 ? L2 : 0;
-            ix += qoff[i];
-            ix -= ix >= L2 ? L2 : 0;
-            v[4 * i + e] = live[i] ? __ldg(src[i] + ix) : 0.0f;
-        }
+        for (int i = 0; i < 2; ++i) v[4 * i + e] = live[i] ? __ldg(src[i] + ix) : 0.0f;
     }
 }
 
@@ -118,7 +116,7 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & (kM - 1), half = tid >> 7;  // class row; position / column half
+    const int row = tid & (kM - 1), part = tid >> 7;  // class row; quad / column part
     const int grp = blockIdx.y;                        // map group
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -159,10 +157,10 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
         const int k_first = c0, k_last = min(c0 + kM, n_cls) - 1;
         const int kb = Q - k - t;
         const bool refl = kb != k && kb != Q;
-        // running sums and compensations of this warp's lanes, its column half
+        // running sums and compensations of this warp's lanes, its column part
 #pragma unroll
-        for (int cc = 0; cc < kN / 2; cc += 16) {
-            const uint32_t col = (uint32_t)(half * (kN / 2) + cc);
+        for (int cc = 0; cc < kN / kParts; cc += 16) {
+            const uint32_t col = (uint32_t)(part * (kN / kParts) + cc);
             tc::tmem_st16(tmem + lane + kColSum + col, zero16);
             tc::tmem_st16(tmem + lane + kColCmp + col, zero16);
         }
@@ -190,29 +188,27 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 }
                 const int P0 = U0 & ~(kKT - 1);
                 const int n_tiles = (U1 - P0) / kKT + 1;
-                // B tile assignment: warp w takes images 2w, 2w+1 (direct for w < 4,
-                // reflected for w >= 4; one hemisphere per warp), lane l positions
-                // 4 (l % 8) .. +3 of rows n = 16 w + l / 8 + 4 i, i = 0..3
+                // B tile assignment: warp w gathers image w (direct for w < 8,
+                // reflected after; north for w % 8 < 4) for the 8 maps: lane l takes
+                // positions 4 (l % 8) .. +3 of rows n = 8 w + l / 8 + 4 i, i = 0, 1
                 // (n = image * kMaps + map): 8 lanes cover a row's 32 positions.
                 const int lane_id = tid & 31;
                 const int pg = lane_id & 7, sub = lane_id >> 3;
-                const bool reflected = warp >= 4;
-                const bool south = ((2 * warp) >> 2) & 1;
+                const bool reflected = warp >= 8;
+                const bool south = (warp >> 2) & 1;
                 const bool b_live_hemi = mirror || !south;
-                const float *src_base[4];
-                int qoff[4];
-                bool live[4];
+                const int qoff = (warp & 3) * Q2;
+                const float *src_base[2];
+                bool live[2];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int n = 16 * warp + sub + 4 * i;
-                    const int im = n / kMaps, mp = grp * kMaps + n % kMaps;
+                for (int i = 0; i < 2; ++i) {
+                    const int mp = grp * kMaps + sub + 4 * i;
                     live[i] = b_live_hemi && mp < n_maps;
                     src_base[i] = live[i] ? in + (long long)mp * map_stride +
                                                 (south ? g.start_m : g.start)
                                           : in;
-                    qoff[i] = (im & 3) * Q2;
                 }
-                float bv[16];  // this lane's B values of the current tile (prefetched)
+                float bv[8];  // this lane's B values of the current tile (prefetched)
                 load_b(src_base, qoff, live, reflected, P0, pg, L2, Q2, g.phase, bv);
                 for (int u = 0; u < n_tiles; ++u) {
                     const int b = tcount & 1;
@@ -223,21 +219,21 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     }
                     Stage &S = stage[b];
                     const int pbase = P0 + u * kKT;
-                    float bn[16];  // next tile's B values: loads in flight during the A build
+                    float bn[8];  // next tile's B values: loads in flight during the A build
                     if (u + 1 < n_tiles)
                         load_b(src_base, qoff, live, reflected, pbase + kKT, pg, L2, Q2, g.phase,
                                bn);
                     if (g.small)
-                        build_a<true>(P, g, S, row, half, pbase, num, L, klo, khi);
+                        build_a<true>(P, g, S, row, part, pbase, num, L, klo, khi);
                     else
-                        build_a<false>(P, g, S, row, half, pbase, num, L, klo, khi);
+                        build_a<false>(P, g, S, row, part, pbase, num, L, klo, khi);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        store_split4(S.b_hi, S.b_lo, tc::toff<kKT>(16 * warp + sub + 4 * i, 4 * pg),
+                    for (int i = 0; i < 2; ++i)
+                        store_split4(S.b_hi, S.b_lo, tc::toff<kKT>(8 * warp + sub + 4 * i, 4 * pg),
                                      make_float4(bv[4 * i], bv[4 * i + 1], bv[4 * i + 2],
                                                  bv[4 * i + 3]));
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) bv[j] = bn[j];
+                    for (int j = 0; j < 8; ++j) bv[j] = bn[j];
                     tc::fence_async_smem();
                     tc::fence_before_sync();
                     __syncthreads();
@@ -280,10 +276,10 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 }
                 tc::fence_after_sync();
                 // Kahan-fold the partial into the running sums (this warp's lanes,
-                // its column half)
+                // its column part)
 #pragma unroll
-                for (int cc = 0; cc < kN / 2; cc += 16) {
-                    const uint32_t col = (uint32_t)(half * (kN / 2) + cc);
+                for (int cc = 0; cc < kN / kParts; cc += 16) {
+                    const uint32_t col = (uint32_t)(part * (kN / kParts) + cc);
                     uint32_t pv[16], sv[16], cv[16];
                     tc::tmem_ld16(tmem + lane + col, pv);
                     tc::tmem_ld16(tmem + lane + kColSum + col, sv);
@@ -305,19 +301,19 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
             }
         }
         if (!ok) break;
-        // outputs of class k: columns n = image * kMaps + map of this thread's half
+        // outputs of class k: columns n = image * kMaps + map of this thread's part
         tc::fence_after_sync();
         const int rs = P.nrings - 1 - r;
         const int start_s = P.d_rings[rs].start;
 #pragma unroll
-        for (int cc = 0; cc < kN / 2; cc += 16) {
+        for (int cc = 0; cc < kN / kParts; cc += 16) {
             uint32_t sv[16];
-            tc::tmem_ld16(tmem + lane + kColSum + (uint32_t)(half * (kN / 2) + cc), sv);
+            tc::tmem_ld16(tmem + lane + kColSum + (uint32_t)(part * (kN / kParts) + cc), sv);
             tc::tmem_wait_ld();
             if (!active) continue;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int n = half * (kN / 2) + cc + j;
+                const int n = part * (kN / kParts) + cc + j;
                 const int im = n / kMaps, mp = grp * kMaps + n % kMaps;
                 const bool s_img = (im >> 2) & 1, r_img = im >> 3;
                 if (mp >= n_maps || (r_img && !refl) || (s_img && !mirror)) continue;
