@@ -36,7 +36,8 @@ namespace {
 constexpr int kM = 128;             // outputs per block (TMEM lanes)
 constexpr int kN = 64;              // maps per group (TMEM columns)
 constexpr int kKT = 32;             // positions per K tile (4 MMAs of K = 8)
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;       // four threads per output row
+constexpr int kParts = kThreads / kM;
 constexpr int kTotStride = kN + 1;  // padded rows: conflict-free per-row access
 constexpr int kTileB = kN * kKT;    // floats per B tile part (hi or lo)
 
@@ -110,6 +111,8 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (kM - 1), part = tid >> 7;  // output row; K-quad / column part
+    constexpr int kCols = kN / kParts;                 // accumulator columns per thread
     const int g = blockIdx.y;  // map group
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -142,9 +145,9 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
         const int2 rg = P.d_range[r];
         const int q_lo = max(rg.x, P.belt_lo), q_hi = min(rg.y, P.belt_hi);
         const PairInfo *pinfo = P.d_pairs + P.d_pair_base[r] - rg.x;
-        for (int n = 0; n < kN; ++n) {
-            tot[tid * kTotStride + n] = 0.0f;
-            cmp[tid * kTotStride + n] = 0.0f;
+        for (int n = part * kCols; n < (part + 1) * kCols; ++n) {
+            tot[row * kTotStride + n] = 0.0f;
+            cmp[row * kTotStride + n] = 0.0f;
         }
         int tcount = 0;
         for (int q = q_lo; q <= q_hi && ok; ++q) {
@@ -209,12 +212,14 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
                         : "memory");
                     copy_b = b;
                 }
-                // A tile row tid: A[m][jj] = w[base + 32 (u - u0) + jj - m]
+                // A tile row `row`, K quads part, part + 4:
+                // A[m][jj] = w[base + 32 (u - u0) + jj - m]
                 {
-                    const int m = tid;
+                    const int m = row;
                     const int wi0 = base + kKT * (u - u0) - m;
 #pragma unroll
-                    for (int jq = 0; jq < kKT; jq += 4) {
+                    for (int jj = 0; jj < (kKT / 4) / kParts; ++jj) {
+                        const int jq = 4 * (part + kParts * jj);
                         float h[4], l[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -275,23 +280,18 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // fold this ring pair's partial (row tid = TMEM lane) into the totals
+            // fold this ring pair's partial (row = TMEM lane, this thread's column
+            // part) into the totals
 #pragma unroll
-            for (int c0 = 0; c0 < kN; c0 += 16) {
+            for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += 16) {
                 uint32_t v[16];
-                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
-                    "%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+                tc::tmem_ld16(ta, v);
+                tc::tmem_wait_ld();
 #pragma unroll
                 for (int jv = 0; jv < 16; ++jv) {
-                    float *s = tot + tid * kTotStride + c0 + jv;
-                    float *cc = cmp + tid * kTotStride + c0 + jv;
+                    float *s = tot + row * kTotStride + c0 + jv;
+                    float *cc = cmp + row * kTotStride + c0 + jv;
                     const float y = __uint_as_float(v[jv]) - *cc;
                     const float tt = *s + y;
                     *cc = (tt - *s) - y;
@@ -301,11 +301,11 @@ conv_belt_mma_kernel(const ConvPlan P, const int2 *__restrict__ items, int n_ite
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
         if (!ok) break;
-        const int k = k0 + tid;
+        const int k = k0 + row;
         if (k < L) {
-            for (int n = 0; n < kN && g * kN + n < n_maps; ++n)
+            for (int n = part * kCols; n < (part + 1) * kCols && g * kN + n < n_maps; ++n)
                 out[(long long)(g * kN + n) * map_stride + R.start + k] =
-                    tot[tid * kTotStride + n] * P.domega;
+                    tot[row * kTotStride + n] * P.domega;
         }
         __syncthreads();
     }
