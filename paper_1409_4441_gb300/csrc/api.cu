@@ -46,6 +46,7 @@ void release(ksc_split *s) {
     cudaFree(s->d_pair_base);
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
+    cudaFree(s->d_items_sym_lpt);
     cudaFree(s->d_items_mma);
     cudaFree(s->d_ws);
     cudaFree(s->d_items_belt);
@@ -216,6 +217,21 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         }
     }
 
+    // The symmetric items longest first, for whole-map launches: CTAs claim items
+    // in list order, so the long items start first and the short ones fill the tail.
+    std::vector<ksc::WorkItem> items_lpt(items_sym);
+    {
+        auto cost = [&](const ksc::WorkItem &w) {
+            const int n_cls = ksc::sym_classes(g.len[w.ring], g.phase[w.ring]);
+            const int cnt = std::min(ksc::sym_chunk(), n_cls - w.k0);
+            return cnt * s->cost_sym[w.ring] * (w.ring == eq ? 1.0 : 2.0);
+        };
+        std::stable_sort(items_lpt.begin(), items_lpt.end(),
+                         [&](const ksc::WorkItem &x, const ksc::WorkItem &y) {
+                             return cost(x) > cost(y);
+                         });
+    }
+
     cudaError_t e;
     cudaGetDevice(&s->device);
     if ((e = dev_upload(&s->d_pairs, pairs.data(), pairs.size())) != cudaSuccess)
@@ -229,6 +245,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     if ((e = dev_upload(&s->d_items, items.data(), items.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
     if ((e = dev_upload(&s->d_items_sym, items_sym.data(), items_sym.size())) != cudaSuccess)
+        return cuda_fail(e, "upload work list");
+    if ((e = dev_upload(&s->d_items_sym_lpt, items_lpt.data(), items_lpt.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
     if ((e = dev_upload(&s->d_items_belt, items_belt.data(), items_belt.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
@@ -376,12 +394,14 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
     if (m0 <= m1) { lo = std::min(lo, m0); hi = std::max(hi, m1); }  // mirror in band
     if (lo <= hi) {
         const int c = s->ring_first_sym[lo], d = s->ring_first_sym[hi + 1];
+        // whole map: the items longest first; a band: its rings' items
+        const ksc::WorkItem *its = whole ? s->d_items_sym_lpt : s->d_items_sym + c;
         if (stack && s->tensor != 1)
-            e = ksc::launch_conv_sym_mma(s->plan, s->d_items_sym + c, d - c, d_in, d_out, n_maps,
-                                         stride, s->n_items_belt > 0 ? 1 : 0, s->d_err, st);
+            e = ksc::launch_conv_sym_mma(s->plan, its, d - c, d_in, d_out, n_maps, stride,
+                                         s->n_items_belt > 0 ? 1 : 0, s->d_err, st);
         else
-            e = ksc::launch_conv_sym(s->plan, s->d_items_sym + c, d - c, d_in, d_out, n_maps,
-                                     stride, s->n_items_belt > 0 ? 1 : 0, r0, r1, st);
+            e = ksc::launch_conv_sym(s->plan, its, d - c, d_in, d_out, n_maps, stride,
+                                     s->n_items_belt > 0 ? 1 : 0, r0, r1, st);
         if (e != cudaSuccess) return cuda_fail(e, "symmetric kernel launch");
     }
     return KSC_OK;
@@ -642,11 +662,11 @@ int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in, float *d
             e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, n_maps,
                                          stride, 0, nullptr, st);
         else if (n_maps >= 16 && s->tensor != 1)
-            e = ksc::launch_conv_sym_mma(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out,
+            e = ksc::launch_conv_sym_mma(s->plan, s->d_items_sym_lpt, s->n_items_sym, d_in, d_out,
                                          n_maps, stride, s->n_items_belt > 0 ? 1 : 0, s->d_err,
                                          st);
         else
-            e = ksc::launch_conv_sym(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out,
+            e = ksc::launch_conv_sym(s->plan, s->d_items_sym_lpt, s->n_items_sym, d_in, d_out,
                                      n_maps, stride, s->n_items_belt > 0 ? 1 : 0, 0,
                                      s->plan.nrings - 1, st);
     } else {
@@ -670,7 +690,7 @@ int ksc_conv_real_stage(const ksc_split *s, const float *d_in, float *d_out, int
             e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, 1, 0, 0,
                                          nullptr, st);
         else
-            e = ksc::launch_conv_sym(s->plan, s->d_items_sym, s->n_items_sym, d_in, d_out, 1, 0,
+            e = ksc::launch_conv_sym(s->plan, s->d_items_sym_lpt, s->n_items_sym, d_in, d_out, 1, 0,
                                      s->n_items_belt > 0 ? 1 : 0, 0, s->plan.nrings - 1, st);
     } else {
         return fail(KSC_ERR_ARG, "stage must be 1 or 2");

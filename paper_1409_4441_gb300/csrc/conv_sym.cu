@@ -270,17 +270,26 @@ __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0
         sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
 }
 
-// One split, items assigned round-robin; grid.y runs over maps.
+// One split; grid.y runs over maps.  CTAs claim items in list order through a
+// counter per map (zero at launch), so the long items of a longest-first list
+// start first and the short ones fill the tail.  (One code path for whole maps
+// and latitude bands keeps their outputs bitwise equal.)
 template <class S>
 __global__ void __launch_bounds__(S::T, S::MINB)
 conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
-                int belt_split, int band_lo, int band_hi) {
+                int belt_split, int band_lo, int band_hi, int *__restrict__ counters) {
     __shared__ SymRing sR[kRingChunk];
     __shared__ __align__(16) float st[kImg * S::kStride];
+    __shared__ int s_next;
     const float *m = in + (long long)blockIdx.y * map_stride;
     float *o = out + (long long)blockIdx.y * map_stride;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    for (;;) {
+        __syncthreads();  // every thread has read the previous claim
+        if (threadIdx.x == 0) s_next = atomicAdd(&counters[blockIdx.y], 1);
+        __syncthreads();
+        const int it = s_next;
+        if (it >= n_items) break;
         const WorkItem w = items[it];
         sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st);
     }
@@ -345,10 +354,19 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
     int blocks = 0;
     cudaError_t e = sym_grid(conv_sym_kernel<S>, S::T, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
-    dim3 grid(blocks, n_maps);
-    conv_sym_kernel<S><<<grid, S::T, 0, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
-                                             belt_split, band_lo, band_hi);
-    return cudaGetLastError();
+    // per-call claim counters, stream-ordered so that calls on several streams
+    // may overlap
+    int *ctr = nullptr;
+    const size_t bytes = sizeof(int) * (size_t)n_maps;
+    if ((e = cudaMallocAsync(&ctr, bytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctr, 0, bytes, st)) == cudaSuccess) {
+        dim3 grid(blocks, n_maps);
+        conv_sym_kernel<S><<<grid, S::T, 0, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
+                                                 belt_split, band_lo, band_hi, ctr);
+        e = cudaGetLastError();
+    }
+    const cudaError_t f = cudaFreeAsync(ctr, st);
+    return e != cudaSuccess ? e : f;
 }
 
 int sym_chunk() { return ShapeFull::kClasses; }

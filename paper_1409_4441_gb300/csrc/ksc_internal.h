@@ -131,6 +131,8 @@ cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_i
 // chunks of sym_chunk().
 int sym_chunk();
 int sym_classes(int len, int phase);  // reflection classes of a ring's first quarter
+// CTAs claim items in list order through per-call counters taken from the
+// stream-ordered allocator.
 cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
                             const float *d_in, float *d_out, int n_maps,
                             long long map_stride, int belt_split, int band_lo,
@@ -199,6 +201,7 @@ struct ksc_split {
     int n_items = 0;
     std::vector<int> ring_first_item;
     ksc::WorkItem *d_items_sym = nullptr;  // northern rings for the symmetric gather
+    ksc::WorkItem *d_items_sym_lpt = nullptr;  // the same items, longest first (whole map)
     int n_items_sym = 0;
     std::vector<int> ring_first_sym;
     int path = 0;                          // 0: belt + symmetric, 1: general only
