@@ -43,6 +43,7 @@ void release(ksc_split *s) {
     cudaFree(s->d_rings);
     cudaFree(s->d_range);
     cudaFree(s->d_pairs);
+    cudaFree(s->d_xinfo);
     cudaFree(s->d_pair_base);
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
@@ -169,6 +170,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     std::vector<int> pair_base(nr + 1, 0);
     for (int r = 0; r < nr; ++r) pair_base[r + 1] = pair_base[r] + (range[r].y - range[r].x + 1);
     std::vector<ksc::PairInfo> pairs((size_t)pair_base[nr]);
+    std::vector<ksc::XInfo> xinfo((size_t)pair_base[nr]);
     {
         const double dc = s->chord_cut;
         const double cos_cut = 1.0 - 0.5 * dc * dc;
@@ -197,6 +199,12 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                     pi.w = (int)std::ceil(dphi * Lq / (2.0 * kPi)) + 1;
                 }
                 pairs[(size_t)pair_base[r] + (q - range[r].x)] = pi;
+                xinfo[(size_t)pair_base[r] + (q - range[r].x)] =
+                    s->theta_cut >= kPi
+                        ? ksc::XInfo{}
+                        : ksc::make_xinfo(A * scale2, 4.0 * ss * scale2,
+                                          kPi / (2.0 * (double)g.len[r] * (double)Lq),
+                                          (double)n_int * (double)n_int, pi.hw, Lq);
             }
         }
     }
@@ -236,6 +244,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     cudaGetDevice(&s->device);
     if ((e = dev_upload(&s->d_pairs, pairs.data(), pairs.size())) != cudaSuccess)
         return cuda_fail(e, "upload ring-pair table");
+    if ((e = dev_upload(&s->d_xinfo, xinfo.data(), xinfo.size())) != cudaSuccess)
+        return cuda_fail(e, "upload ring-pair x tables");
     if ((e = dev_upload(&s->d_pair_base, pair_base.data(), pair_base.size())) != cudaSuccess)
         return cuda_fail(e, "upload ring-pair offsets");
     if ((e = dev_upload(&s->d_rings, rings.data(), rings.size())) != cudaSuccess)
@@ -283,6 +293,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     p.d_rings = s->d_rings;
     p.d_range = s->d_range;
     p.d_pairs = s->d_pairs;
+    p.d_xinfo = s->d_xinfo;
     p.d_pair_base = s->d_pair_base;
     p.d_tab = s->d_tab;
     p.n_int = n_int;
@@ -411,6 +422,38 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
 
 namespace ksc {
 void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq) {
+    XInfo x{};
+    // no pair within the cut, or a whole-ring window: no table
+    if (hw < 0.0f || 2.0f * hw + 3.0f >= (float)lq || A2 >= nint2 || B2 <= 0.0) return x;
+    const double sx2 = (nint2 - A2) / B2;  // sin^2 of x at the cut
+    if (sx2 >= 1.0) return x;
+    const double xcut = std::asin(std::sqrt(sx2));
+    // largest du/dx on [0, xcut]: u^2 = A2 + B2 S, S = sin^2 x, du/dx = B2 sqrt(g(S)) with
+    // g = S (1 - S) / (A2 + B2 S), unimodal in S with its peak where B2 S^2 + 2 A2 S = A2
+    double dmax;
+    if (A2 <= 0.0) {
+        dmax = std::sqrt(B2);  // u = sqrt(B2) sin x
+    } else {
+        double S = (-A2 + std::sqrt(A2 * A2 + A2 * B2)) / B2;
+        S = std::min(std::max(S, 0.0), sx2);
+        dmax = B2 * std::sqrt(S * (1.0 - S) / (A2 + B2 * S));
+    }
+    if (!(dmax > 0.0)) return x;
+    const double dx = std::max(kXRho / dmax, xcut / (kXCap - 2.0));
+    const double cells = std::floor(xcut / dx) + 2.0;  // in-cut positions stay below ncell - 1
+    if (cells > (double)kXCap || dx * dmax > kXRhoMax || cells * dx > 0.5 * kPi + 0.05) return x;
+    const DF dxd = df_from_double(dx), R = df_from_double(c / dx);
+    x.dxh = dxd.h;
+    x.dxl = dxd.l;
+    x.Rh = R.h;
+    x.Rl = R.l;
+    x.ncut = (float)std::floor(xcut / c);
+    x.ncell = (int)cells;
+    x.pmax = (float)cells - 0.5f;
+    return x;
+}
 } // namespace ksc
 
 extern "C" {

@@ -43,15 +43,19 @@ constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, refle
 // Tile shape: T threads, LANES lanes per reflection class (1, or 2 for paired
 // lanes), SPAN staged input positions per segment (each image row padded by 4
 // floats), MINB resident CTAs per SM the register budget is set for.
-template <int T_, int LANES_, int SPAN_, int MINB_> struct SymShape {
+// XCAP: x-table cells held in dynamic shared memory (0: weights evaluated
+// directly for every pair).
+template <int T_, int LANES_, int SPAN_, int MINB_, int XCAP_> struct SymShape {
     static constexpr int T = T_, LANES = LANES_, kSpan = SPAN_, MINB = MINB_;
     static constexpr int kStride = SPAN_ + 4;
     static constexpr int kClasses = T_ / LANES_;      // classes per item
     static constexpr int kImgT = kImg / LANES_;       // images per thread
+    static constexpr int kXCap = XCAP_;
+    static constexpr size_t kDynSmem = sizeof(float4) * (size_t)XCAP_;
 };
-using ShapeFull = SymShape<128, 1, 512, 3>;   // variant 0
-using ShapeHalf = SymShape<64, 1, 256, 6>;    // variant 1
-using ShapePair = SymShape<128, 2, 384, 5>;   // variant 2
+using ShapeFull = SymShape<128, 1, 512, 3, kXCap>;  // variant 0
+using ShapeHalf = SymShape<64, 1, 256, 6, 0>;       // variant 1
+using ShapePair = SymShape<128, 2, 384, 5, 0>;      // variant 2
 
 __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
     const float y = v - *comp;
@@ -71,10 +75,13 @@ __device__ __forceinline__ int img_row(int i, int lanes, int h) {
 // The four kernel weights of quad kq (positions kq .. kq + 3; zero outside
 // [a, b] and beyond the cut).  With paired lanes each lane evaluates two and
 // the pair swaps them.  Straight-line code: the evaluations interleave.
-template <class S, bool SMALL>
-__device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing &g, int kq, int a,
-                                               int b, long long num, int L, int h,
-                                               unsigned pair_mask) {
+// MODE 0: double-float chord with the general sine; 1: with the small-angle
+// sine; 2: the ring pair's x table (partial windows only: every position
+// outside [a, b] then lies beyond the cut, so the cut test alone zeroes it).
+template <class S, int MODE>
+__device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing &g,
+                                               const float4 *xt, int kq, int a, int b,
+                                               long long num, int L, int h, unsigned pair_mask) {
     const float N0 = (float)(num - 2LL * kq * L);  // exact integer below 2^24
     const float step = (float)(2 * L);
     float w[4];
@@ -82,7 +89,11 @@ __device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing 
 #pragma unroll
     for (int ee = 0; ee < NE; ++ee) {
         const int e = S::LANES == 2 ? 2 * h + ee : ee;
-        w[ee] = sym_weight<SMALL>(P, g, N0 - (float)e * step, kq + e, a, b);
+        const float Nf = N0 - (float)e * step;
+        if constexpr (MODE == 2)
+            w[ee] = xtab_weight(xt, g, Nf);
+        else
+            w[ee] = sym_weight<MODE == 1>(P, g, Nf, kq + e, a, b);
     }
     if constexpr (S::LANES == 2) {  // swap halves with the partner lane
         const float o0 = __shfl_xor_sync(pair_mask, w[0], 1);
@@ -97,10 +108,10 @@ __device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing 
 // loop is software-pipelined: the weights of the next quad are evaluated
 // while the current quad's weights feed the FFMAs, so the long double-float
 // chains overlap the multiply-adds.
-template <class S, bool MIRROR, bool SMALL>
-__device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float *st,
-                                           int s0, int a, int b, long long num, int L,
-                                           float *sum, float *comp) {
+template <class S, bool MIRROR, int MODE>
+__device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float4 *xt,
+                                           const float *st, int s0, int a, int b, long long num,
+                                           int L, float *sum, float *comp) {
     constexpr int kStride = S::kStride, NI = S::kImgT;
     const int h = S::LANES == 2 ? (threadIdx.x & 1) : 0;
     const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1);
@@ -111,10 +122,10 @@ __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, 
     int nq = 0;
     int kq = s0 + ((a - s0) & ~3);
     if (kq > b) return;
-    float4 wc = quad_weights<S, SMALL>(P, g, kq, a, b, num, L, h, pair_mask);
+    float4 wc = quad_weights<S, MODE>(P, g, xt, kq, a, b, num, L, h, pair_mask);
     for (; kq <= b; kq += 4) {
         // next quad's weights (past b they are zero and unused)
-        const float4 wn = quad_weights<S, SMALL>(P, g, kq + 4, a, b, num, L, h, pair_mask);
+        const float4 wn = quad_weights<S, MODE>(P, g, xt, kq + 4, a, b, num, L, h, pair_mask);
         const int j = kq - s0;
         if (!idle) {
 #pragma unroll
@@ -144,11 +155,34 @@ __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, 
     for (int i = 0; i < NI; ++i) kahan(&sum[i], &comp[i], part[i]);
 }
 
+// The x table of ring pair g in shared memory: cell j holds the cubic
+// coefficients (in the cell offset) from the weights and slopes at boundaries j
+// and j + 1.  Each thread fills a run of consecutive cells, so every boundary
+// but the run's first is evaluated once.
+template <class S>
+__device__ __forceinline__ void build_xtab(const ConvPlan &P, const SymRing &g, float4 *xt) {
+    const int per = (g.ncell + S::T - 1) / S::T;
+    const int j0 = threadIdx.x * per, j1 = min(j0 + per, g.ncell);
+    if (j0 >= j1) return;
+    float w0, d0;
+    xtab_node(P, g, j0, &w0, &d0);
+    for (int j = j0; j < j1; ++j) {
+        float w1, d1;
+        xtab_node(P, g, j + 1, &w1, &d1);
+        const float dw = w1 - w0;
+        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
+                            fmaf(-2.0f, dw, d0 + d1));
+        w0 = w1;
+        d0 = d1;
+    }
+}
+
 template <class S, bool MIRROR>
 __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n_cls,
                                          bool skip_belt_inputs, bool add, int band_lo,
                                          int band_hi, const float *__restrict__ m,
-                                         float *__restrict__ o, SymRing *sR, float *st) {
+                                         float *__restrict__ o, SymRing *sR, float *st,
+                                         float4 *xt) {
     constexpr int T = S::T, kSpan = S::kSpan, kStride = S::kStride, NI = S::kImgT;
     const int tid = threadIdx.x;
     const int h = S::LANES == 2 ? (tid & 1) : 0;  // paired lanes: hemisphere
@@ -179,6 +213,11 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             sym_window(k, t, L, g, &num, &klo, &khi);
             sym_window(k_first, t, L, g, &numx, &U0, &dummy);
             sym_window(k_last, t, L, g, &numx, &dummy, &U1);
+            const bool use_xt = S::kXCap > 0 && g.ncell > 0 && g.ncell <= S::kXCap;
+            if (use_xt) {  // (the segment's first barrier publishes the table)
+                __syncthreads();  // the previous ring pair's lookups are done
+                build_xtab<S>(P, g, xt);
+            }
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 // positions this segment needs (the union ends at U1)
                 const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
@@ -207,10 +246,12 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 if (a > b) continue;
                 // (classes without a reflection partner accumulate the reflected
                 // images too; those sums are never written)
-                if (g.small)
-                    accumulate<S, MIRROR, true>(P, g, st, s0, a, b, num, L, sum, comp);
+                if (S::kXCap > 0 && use_xt)
+                    accumulate<S, MIRROR, 2>(P, g, xt, st, s0, a, b, num, L, sum, comp);
+                else if (g.small)
+                    accumulate<S, MIRROR, 1>(P, g, xt, st, s0, a, b, num, L, sum, comp);
                 else
-                    accumulate<S, MIRROR, false>(P, g, st, s0, a, b, num, L, sum, comp);
+                    accumulate<S, MIRROR, 0>(P, g, xt, st, s0, a, b, num, L, sum, comp);
             }
         }
     }
@@ -257,7 +298,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
 template <class S>
 __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0, int belt_split,
                                              int band_lo, int band_hi, const float *m, float *o,
-                                             SymRing *sR, float *st) {
+                                             SymRing *sR, float *st, float4 *xt) {
     const int eq = (P.nrings - 1) / 2;  // the equator ring, its own mirror image
     const DevRing R = P.d_rings[ring];
     const int Q = R.len / 4;
@@ -265,9 +306,9 @@ __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0
     const bool belt = ring >= P.belt_lo && ring <= P.belt_hi;
     const bool add = belt_split && belt;
     if (ring == eq)
-        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt);
     else
-        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st);
+        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt);
 }
 
 // One split; grid.y runs over maps.  CTAs claim items in list order through a
@@ -282,6 +323,7 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
     __shared__ SymRing sR[kRingChunk];
     __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
+    extern __shared__ float4 xt[];  // S::kXCap cells
     const float *m = in + (long long)blockIdx.y * map_stride;
     float *o = out + (long long)blockIdx.y * map_stride;
     for (;;) {
@@ -291,7 +333,7 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
         const int it = s_next;
         if (it >= n_items) break;
         const WorkItem w = items[it];
-        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st);
+        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st, xt);
     }
 }
 
@@ -304,6 +346,7 @@ conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__re
     __shared__ SymRing sR[kRingChunk];
     __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
+    extern __shared__ float4 xt[];  // S::kXCap cells
     for (;;) {
         __syncthreads();  // every thread has read the previous claim
         if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
@@ -313,7 +356,7 @@ conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__re
         const int4 w = items[it];
         const BatchEntry e = entries[w.x];
         const ConvPlan &P = plans[e.plan];
-        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st);
+        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st, xt);
     }
 }
 
@@ -328,10 +371,18 @@ int sm_count_sym() {
     return n_sm;
 }
 
+// Grid of a persistent launch; the kernel's dynamic shared memory (the x table)
+// is enabled on first use.
 template <class K>
-cudaError_t sym_grid(K kernel, int threads, int n_items, int per_sm_cap, int *blocks) {
+cudaError_t sym_grid(K kernel, int threads, size_t dyn_smem, int n_items, int per_sm_cap,
+                     int *blocks) {
+    cudaError_t e;
+    if (dyn_smem > 0 &&
+        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)dyn_smem)) != cudaSuccess)
+        return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn_smem);
     if (e != cudaSuccess) return e;
     if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
     if (per_sm < 1) per_sm = 1;
@@ -352,7 +403,7 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
     using S = ShapeFull;
     int blocks = 0;
-    cudaError_t e = sym_grid(conv_sym_kernel<S>, S::T, n_items, 0, &blocks);
+    cudaError_t e = sym_grid(conv_sym_kernel<S>, S::T, S::kDynSmem, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
     // per-call claim counters, stream-ordered so that calls on several streams
     // may overlap
@@ -361,8 +412,9 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
     if ((e = cudaMallocAsync(&ctr, bytes, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ctr, 0, bytes, st)) == cudaSuccess) {
         dim3 grid(blocks, n_maps);
-        conv_sym_kernel<S><<<grid, S::T, 0, st>>>(p, d_items, n_items, d_in, d_out, map_stride,
-                                                 belt_split, band_lo, band_hi, ctr);
+        conv_sym_kernel<S><<<grid, S::T, S::kDynSmem, st>>>(p, d_items, n_items, d_in, d_out,
+                                                           map_stride, belt_split, band_lo,
+                                                           band_hi, ctr);
         e = cudaGetLastError();
     }
     const cudaError_t f = cudaFreeAsync(ctr, st);
@@ -383,10 +435,11 @@ cudaError_t sym_batch_launch(const ConvPlan *d_plans, const BatchEntry *d_entrie
                              const int4 *d_items, int n_items, int per_sm_cap, int *d_counter,
                              cudaStream_t st) {
     int blocks = 0;
-    cudaError_t e = sym_grid(conv_sym_batch_kernel<S>, S::T, n_items, per_sm_cap, &blocks);
+    cudaError_t e =
+        sym_grid(conv_sym_batch_kernel<S>, S::T, S::kDynSmem, n_items, per_sm_cap, &blocks);
     if (e != cudaSuccess) return e;
-    conv_sym_batch_kernel<S><<<blocks, S::T, 0, st>>>(d_plans, d_entries, d_items, n_items,
-                                                      d_counter);
+    conv_sym_batch_kernel<S><<<blocks, S::T, S::kDynSmem, st>>>(d_plans, d_entries, d_items,
+                                                                n_items, d_counter);
     return cudaGetLastError();
 }
 

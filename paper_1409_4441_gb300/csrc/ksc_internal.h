@@ -38,6 +38,29 @@ struct PairInfo {
     int w;
 };
 
+// Weight table of one ring pair for the symmetric gather.  For a fixed ring
+// pair the kernel weight depends on the pixel pair only through
+// x = dphi / 2 = |N| c, so it is tabulated in x: ncell cubic cells of width dx
+// (kXRho table intervals of the chord each at most, stretched up to kXRhoMax
+// where that many cells would not fit a CTA's kXCap), cell position
+// p = |N| c / dx = |N| R.  Pairs with |N| <= ncut lie within the cut.
+// ncell = 0: no table (whole-ring windows, or more cells than a CTA holds).
+struct XInfo {
+    float dxh, dxl;  // dx as a double-float pair
+    float Rh, Rl;    // R = c / dx as a double-float pair
+    float ncut;      // largest |N| within the cut (an exact integer)
+    float pmax;      // ncell - 0.5: cell positions are clamped below it
+    int ncell, pad;
+};
+constexpr double kXRho = 2.0;     // chord-table intervals per x cell (at most) ...
+constexpr double kXRhoMax = 3.0;  // ... unless the cells would not fit
+constexpr int kXCap = 2048;    // cells a CTA holds in shared memory (32 kB)
+
+// Host: the x-table parameters of ring pair (r, q); A2, B2 are the ring-pair
+// constants scaled to table-position units, lq the input ring's length, hw the
+// window half-width (whole-ring windows get no table).
+XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq);
+
 // ---------------------------------------------------------------------------
 // Host FP64 split fit (Sec. 2, Eq. 1-6).
 // ---------------------------------------------------------------------------
@@ -85,6 +108,7 @@ struct ConvPlan {
     const DevRing *d_rings;  // nrings
     const int2 *d_range;     // per output ring: first/last input ring (0-based)
     const PairInfo *d_pairs; // ring-pair geometry, d_pair_base[r] + (q - range.x)
+    const XInfo *d_xinfo;    // x tables of the symmetric gather, same indexing
     const int *d_pair_base;
     const float4 *d_tab;     // table
     int n_int;
@@ -195,6 +219,7 @@ struct ksc_split {
     ksc::DevRing *d_rings = nullptr;
     int2 *d_range = nullptr;
     ksc::PairInfo *d_pairs = nullptr;
+    ksc::XInfo *d_xinfo = nullptr;
     int *d_pair_base = nullptr;
     // work lists, each with a per-ring prefix (nrings + 1 offsets)
     ksc::WorkItem *d_items = nullptr;   // every ring (pair counting)

@@ -18,6 +18,9 @@ struct SymRing {  // one (output ring, input ring) pair
     DF A, B, c;
     float hw;     // half window in input pixels; < 0: no pixel within the cut
     int len, start, start_m, phase, small;
+    DF dx, R;     // x table (XInfo): cell width, cell position per unit |N|
+    float ncut, pmax;
+    int ncell;    // 0: no x table
 };
 
 __device__ __forceinline__ int sym_pmod(int a, int n) {
@@ -43,6 +46,12 @@ __device__ __forceinline__ SymRing load_sym_ring(const ConvPlan &P, int r, int q
     // |dphi / 2| < 0.25 over the whole (partial) window: the cheap sine
     g.small = (2.0f * pi.hw + 3.0f < (float)Qr.len) &&
               ((pi.hw + 1.0f) * 3.14159265f / (float)Qr.len < 0.25f);
+    const XInfo xi = P.d_xinfo[P.d_pair_base[r] + (q - rg.x)];
+    g.dx = DF{xi.dxh, xi.dxl};
+    g.R = DF{xi.Rh, xi.Rl};
+    g.ncut = xi.ncut;
+    g.pmax = xi.pmax;
+    g.ncell = g.hw < 0.0f ? 0 : xi.ncell;
     return g;
 }
 
@@ -83,6 +92,52 @@ __device__ __forceinline__ float sym_weight(const ConvPlan &P, const SymRing &g,
     const bool in = chord_to_table_sel(g.A, g.B, sn, P.nint2, &ti, &f);
     const float wv = hermite(__ldg(&P.d_tab[min(ti, P.n_int)]), f);
     return (in && kp >= a && kp <= b) ? wv : 0.0f;
+}
+
+// x table of one ring pair (XInfo): the weight at cell boundary j, x = j dx,
+// and its slope per cell, from the same double-float chord and K_r table as
+// sym_weight.  Boundaries past the cut extrapolate the table's last cubic, so
+// the cell that holds the cut interpolates a smooth function.
+__device__ __forceinline__ void xtab_node(const ConvPlan &P, const SymRing &g, int j, float *w,
+                                          float *d) {
+    const float jf = (float)j;
+    const float xh = jf * g.dx.h;
+    const float xl = fmaf(jf, g.dx.h, -xh) + jf * g.dx.l;
+    const DF s = sin_df(xh, xl);
+    const float s2h = s.h * s.h;
+    const float s2l = fmaf(2.0f * s.h, s.l, fmaf(s.h, s.h, -s2h));
+    const float ph = g.B.h * s2h;
+    const float pl = fmaf(g.B.h, s2h, -ph) + fmaf(g.B.h, s2l, g.B.l * s2h);
+    const float dh = g.A.h + ph;
+    const float bp = dh - g.A.h;
+    const float e = (g.A.h - (dh - bp)) + (ph - bp);
+    const float dl = e + g.A.l + pl;
+    const float rr = rsqrtf(fmaxf(dh, 1e-30f));
+    const float uh = dh * rr;
+    const float ul = (fmaf(-uh, uh, dh) + dl) * (0.5f * rr);
+    const int i = max(0, min((int)floorf(uh), P.n_int - 1));
+    const float f = (uh - (float)i) + ul;
+    const float4 c = __ldg(&P.d_tab[i]);
+    *w = hermite(c, f);
+    const float dk = fmaf(f, fmaf(f, 3.0f * c.w, 2.0f * c.z), c.y);  // dK/du
+    // (the slope needs no more than the fast cosine: absolute error ~5e-7)
+    const float dudx = g.B.h * s.h * __cosf(xh) / fmaxf(uh, 1e-30f);
+    *d = dk * dudx * g.dx.h;
+}
+
+// Weight of the pixel pair with exact integer Nf from the x table xt (cubic
+// coefficients per cell); zero beyond the cut.
+__device__ __forceinline__ float xtab_weight(const float4 *xt, const SymRing &g, float Nf) {
+    const float an = fabsf(Nf);
+    const float ph = an * g.R.h;
+    const float pl = fmaf(an, g.R.l, fmaf(an, g.R.h, -ph));
+    const float pc = fminf(ph, g.pmax);
+    const float t = (pc - 0.5f) + 12582912.0f;  // floor by the 1.5 * 2^23 rounding trick
+    const int j = __float_as_int(t) - 0x4B400000;
+    const float f = (pc - (t - 12582912.0f)) + pl;
+    const float4 c = xt[j];
+    const float v = hermite(c, f);
+    return an <= g.ncut ? v : 0.0f;
 }
 
 } // namespace ksc
