@@ -53,7 +53,7 @@ template <int T_, int LANES_, int SPAN_, int MINB_, int XCAP_> struct SymShape {
     static constexpr int kXCap = XCAP_;
     static constexpr size_t kDynSmem = sizeof(float4) * (size_t)XCAP_;
 };
-using ShapeFull = SymShape<128, 1, 512, 3, kXCap>;  // variant 0
+using ShapeFull = SymShape<128, 1, 384, 4, kXCap>;  // variant 0
 using ShapeHalf = SymShape<64, 1, 256, 6, 0>;       // variant 1
 using ShapePair = SymShape<128, 2, 384, 5, 0>;      // variant 2
 
@@ -161,7 +161,8 @@ __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, 
 // but the run's first is evaluated once.
 template <class S>
 __device__ __forceinline__ void build_xtab(const ConvPlan &P, const SymRing &g, float4 *xt) {
-    const int per = (g.ncell + S::T - 1) / S::T;
+    // an odd run length keeps the 16-byte stores of a warp on distinct banks
+    const int per = ((g.ncell + S::T - 1) / S::T) | 1;
     const int j0 = threadIdx.x * per, j1 = min(j0 + per, g.ncell);
     if (j0 >= j1) return;
     float w0, d0;

@@ -61,9 +61,13 @@ __device__ __forceinline__ void store_split4(float *hi, float *lo, int off, floa
 // quads wholly outside the window are zero without evaluation (the tiles span
 // the union of 128 classes' windows, whose ends shift by about one position
 // per class, so the branch is uniform across a warp except near the ends).
-template <bool SMALL>
-__device__ __forceinline__ void build_a(const ConvPlan &P, const SymRing &g, Stage &S, int row,
-                                        int part, int pbase, long long num, int L, int a, int b) {
+// MODE 0 / 1: double-float chord (general / small-angle sine); 2: the ring
+// pair's x table xt (partial windows: positions outside [a, b] lie beyond the
+// cut, which the table's cut test zeroes).
+template <int MODE>
+__device__ __forceinline__ void build_a(const ConvPlan &P, const SymRing &g, const float4 *xt,
+                                        Stage &S, int row, int part, int pbase, long long num,
+                                        int L, int a, int b) {
     const float step = (float)(2 * L);
 #pragma unroll
     for (int j = 0; j < (kKT / 4) / kParts; ++j) {
@@ -77,11 +81,37 @@ __device__ __forceinline__ void build_a(const ConvPlan &P, const SymRing &g, Sta
         }
         const float N0 = (float)(num - 2LL * kq * L);
         float4 w;
-        w.x = sym_weight<SMALL>(P, g, N0, kq, a, b);
-        w.y = sym_weight<SMALL>(P, g, N0 - step, kq + 1, a, b);
-        w.z = sym_weight<SMALL>(P, g, N0 - 2.0f * step, kq + 2, a, b);
-        w.w = sym_weight<SMALL>(P, g, N0 - 3.0f * step, kq + 3, a, b);
+        if constexpr (MODE == 2) {
+            w.x = xtab_weight(xt, g, N0);
+            w.y = xtab_weight(xt, g, N0 - step);
+            w.z = xtab_weight(xt, g, N0 - 2.0f * step);
+            w.w = xtab_weight(xt, g, N0 - 3.0f * step);
+        } else {
+            w.x = sym_weight<MODE == 1>(P, g, N0, kq, a, b);
+            w.y = sym_weight<MODE == 1>(P, g, N0 - step, kq + 1, a, b);
+            w.z = sym_weight<MODE == 1>(P, g, N0 - 2.0f * step, kq + 2, a, b);
+            w.w = sym_weight<MODE == 1>(P, g, N0 - 3.0f * step, kq + 3, a, b);
+        }
         store_split4(S.a_hi, S.a_lo, o, w);
+    }
+}
+
+// The ring pair's x table (cubic coefficients per cell), all threads of the CTA
+// filling runs of consecutive cells (odd run length: distinct banks).
+__device__ __forceinline__ void build_xtab_mma(const ConvPlan &P, const SymRing &g, float4 *xt) {
+    const int per = ((g.ncell + kThreads - 1) / kThreads) | 1;
+    const int j0 = threadIdx.x * per, j1 = min(j0 + per, g.ncell);
+    if (j0 >= j1) return;
+    float w0, d0;
+    xtab_node(P, g, j0, &w0, &d0);
+    for (int j = j0; j < j1; ++j) {
+        float w1, d1;
+        xtab_node(P, g, j + 1, &w1, &d1);
+        const float dw = w1 - w0;
+        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
+                            fmaf(-2.0f, dw, d0 + d1));
+        w0 = w1;
+        d0 = d1;
     }
 }
 
@@ -110,13 +140,20 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     long long map_stride, int belt_split, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Stage *stage = reinterpret_cast<Stage *>(smem_raw);  // 2 stages
+    float4 *xt = reinterpret_cast<float4 *>(smem_raw + 2 * sizeof(Stage));  // kXCap cells
     __shared__ SymRing sR[kRingChunk];
     __shared__ __align__(8) uint64_t mdone[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & (kM - 1), part = tid >> 7;  // class row; quad / column part
+    // Epilogue (tensor memory) mapping: a warp reaches TMEM lanes 32 (warp % 4) ..
+    // + 31, so warp w holds class rows 32 (w % 4) .. and column part w / 4.
+    const int row = tid & (kM - 1), part = tid >> 7;
+    // A-tile mapping: warp w builds rows 32 (w / 4) .. + 31, quads part w % 4, so
+    // each scheduler (warps w = s mod 4) holds every row block and the rows whose
+    // windows miss a tile (at the ends of the union) spread over all schedulers.
+    const int brow = (tid & 31) + 32 * (warp >> 2), bpart = warp & 3;
     const int grp = blockIdx.y;                        // map group
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -154,6 +191,7 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
         const bool add = belt_split && r >= P.belt_lo && r <= P.belt_hi;
         const int k = c0 + row;
         const bool active = k < n_cls;
+        const int kbld = c0 + brow;  // class of the A-tile row this thread builds
         const int k_first = c0, k_last = min(c0 + kM, n_cls) - 1;
         const int kb = Q - k - t;
         const bool refl = kb != k && kb != Q;
@@ -179,12 +217,17 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 const int L2 = g.len, Q2 = L2 / 4;
                 long long num, numx;
                 int klo, khi, U0, U1, dummy;
-                sym_window(k, t, L, g, &num, &klo, &khi);
+                sym_window(kbld, t, L, g, &num, &klo, &khi);
                 sym_window(k_first, t, L, g, &numx, &U0, &dummy);
                 sym_window(k_last, t, L, g, &numx, &dummy, &U1);
-                if (!active) {  // empty window: zero weights
+                if (kbld >= n_cls) {  // empty window: zero weights
                     klo = 1;
                     khi = 0;
+                }
+                const bool use_xt = g.ncell > 0 && g.ncell <= kXCap;
+                if (use_xt) {  // (the previous ring pair ended at a barrier)
+                    build_xtab_mma(P, g, xt);
+                    __syncthreads();
                 }
                 const int P0 = U0 & ~(kKT - 1);
                 const int n_tiles = (U1 - P0) / kKT + 1;
@@ -223,10 +266,12 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     if (u + 1 < n_tiles)
                         load_b(src_base, qoff, live, reflected, pbase + kKT, pg, L2, Q2, g.phase,
                                bn);
-                    if (g.small)
-                        build_a<true>(P, g, S, row, part, pbase, num, L, klo, khi);
+                    if (use_xt)
+                        build_a<2>(P, g, xt, S, brow, bpart, pbase, num, L, klo, khi);
+                    else if (g.small)
+                        build_a<1>(P, g, xt, S, brow, bpart, pbase, num, L, klo, khi);
                     else
-                        build_a<false>(P, g, S, row, part, pbase, num, L, klo, khi);
+                        build_a<0>(P, g, xt, S, brow, bpart, pbase, num, L, klo, khi);
 #pragma unroll
                     for (int i = 0; i < 2; ++i)
                         store_split4(S.b_hi, S.b_lo, tc::toff<kKT>(8 * warp + sub + 4 * i, 4 * pg),
@@ -355,7 +400,7 @@ cudaError_t launch_conv_sym_mma(const ConvPlan &p, const WorkItem *d_items, int 
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (n_sm <= 0) n_sm = 1;
     }
-    const size_t smem = 2 * sizeof(Stage);
+    const size_t smem = 2 * sizeof(Stage) + sizeof(float4) * kXCap;
     cudaError_t e = cudaFuncSetAttribute(conv_sym_mma_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

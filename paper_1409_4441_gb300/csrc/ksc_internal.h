@@ -54,7 +54,7 @@ struct XInfo {
 };
 constexpr double kXRho = 2.0;     // chord-table intervals per x cell (at most) ...
 constexpr double kXRhoMax = 3.0;  // ... unless the cells would not fit
-constexpr int kXCap = 2048;    // cells a CTA holds in shared memory (32 kB)
+constexpr int kXCap = 1792;    // cells a CTA holds in shared memory (28 kB)
 
 // Host: the x-table parameters of ring pair (r, q); A2, B2 are the ring-pair
 // constants scaled to table-position units, lq the input ring's length, hw the
