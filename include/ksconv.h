@@ -87,6 +87,13 @@ typedef struct {
                           fit is unconstrained and K_r may jump at the cut
                           (a jump leaves a pixel-sum error on smooth maps of
                           about |K_r(theta_cut)| x boundary pixels)          */
+    int exact_weights; /* 0 (default): the cap ring pairs' kernel weights come
+                          from a per-ring-pair cubic table in dphi / 2 (cells
+                          of at most 2-3 intervals of the K_r table, built per
+                          work item in shared memory; interpolation error
+                          at most 3e-7 of the kernel's peak, rms about 1e-8);
+                          1: every weight from the double-float chord and
+                          the K_r table                                      */
 } ksc_split_opts;
 
 #define KSC_CUT_C1 0

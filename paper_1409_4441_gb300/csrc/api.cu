@@ -62,12 +62,12 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     const int nside = s->nside;
     s->chord_cut = 2.0 * std::sin(0.5 * s->theta_cut);
     int n_int = o.n_intervals;
+    // ~96 intervals per shortest l_max wavelength; the chord compresses
+    // theta by cos(theta/2), so wide cuts need proportionally more
+    const double squeeze = std::max(std::cos(0.5 * s->theta_cut), 1e-3);
+    const double n_auto = 96.0 * s->chord_cut * std::max(s->lmax, 1) / (2.0 * kPi * squeeze);
     if (n_int <= 0) {
-        // ~96 intervals per shortest l_max wavelength; the chord compresses
-        // theta by cos(theta/2), so wide cuts need proportionally more
-        const double squeeze = std::max(std::cos(0.5 * s->theta_cut), 1e-3);
-        double want = 96.0 * s->chord_cut * std::max(s->lmax, 1) / (2.0 * kPi * squeeze);
-        n_int = (int)std::ceil(want);
+        n_int = (int)std::ceil(n_auto);
         n_int = std::max(256, std::min(n_int, ksc::kMaxIntervals));
     }
     if (n_int > ksc::kMaxIntervals) return fail(KSC_ERR_ARG, "n_intervals above 8192");
@@ -176,6 +176,9 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         const double cos_cut = 1.0 - 0.5 * dc * dc;
         const double scale2 = ((double)n_int / dc) * ((double)n_int / dc);
         const double dc2 = s->theta_cut >= kPi ? 5.0 : dc * dc;
+        // x cells are sized in intervals of the automatic table size, so a coarser
+        // user table gets proportionally narrower cells (in its own intervals)
+        const double xscale = std::min(1.0, (double)n_int / std::max(n_auto, 1.0));
 #pragma omp parallel for schedule(dynamic, 16)
         for (int r = 0; r < nr; ++r) {
             for (int q = range[r].x; q <= range[r].y; ++q) {
@@ -200,11 +203,11 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                 }
                 pairs[(size_t)pair_base[r] + (q - range[r].x)] = pi;
                 xinfo[(size_t)pair_base[r] + (q - range[r].x)] =
-                    s->theta_cut >= kPi
+                    (s->theta_cut >= kPi || o.exact_weights)
                         ? ksc::XInfo{}
                         : ksc::make_xinfo(A * scale2, 4.0 * ss * scale2,
                                           kPi / (2.0 * (double)g.len[r] * (double)Lq),
-                                          (double)n_int * (double)n_int, pi.hw, Lq);
+                                          (double)n_int * (double)n_int, pi.hw, Lq, xscale);
             }
         }
     }
@@ -337,6 +340,7 @@ ksc_split_opts resolve_opts(const ksc_split_opts *opts) {
         if (o.tensor != 1 && o.tensor != 2) o.tensor = 0;
         if (o.cut_continuity < KSC_CUT_C1 || o.cut_continuity > KSC_CUT_FREE)
             o.cut_continuity = KSC_CUT_C1;
+        if (o.exact_weights != 1) o.exact_weights = 0;
     }
     return o;
 }
@@ -423,7 +427,7 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
 namespace ksc {
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 
-XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq) {
+XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq, double scale) {
     XInfo x{};
     // no pair within the cut, or a whole-ring window: no table
     if (hw < 0.0f || 2.0f * hw + 3.0f >= (float)lq || A2 >= nint2 || B2 <= 0.0) return x;
@@ -441,9 +445,10 @@ XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq)
         dmax = B2 * std::sqrt(S * (1.0 - S) / (A2 + B2 * S));
     }
     if (!(dmax > 0.0)) return x;
-    const double dx = std::max(kXRho / dmax, xcut / (kXCap - 2.0));
+    const double dx = std::max(scale * kXRho / dmax, xcut / (kXCap - 2.0));
     const double cells = std::floor(xcut / dx) + 2.0;  // in-cut positions stay below ncell - 1
-    if (cells > (double)kXCap || dx * dmax > kXRhoMax || cells * dx > 0.5 * kPi + 0.05) return x;
+    if (cells > (double)kXCap || dx * dmax > scale * kXRhoMax || cells * dx > 0.5 * kPi + 0.05)
+        return x;
     const DF dxd = df_from_double(dx), R = df_from_double(c / dx);
     x.dxh = dxd.h;
     x.dxl = dxd.l;
@@ -468,6 +473,7 @@ int ksc_default_opts(ksc_split_opts *opts) {
     opts->path = 0;
     opts->tensor = 0;
     opts->cut_continuity = KSC_CUT_C1;
+    opts->exact_weights = 0;
     return KSC_OK;
 }
 

@@ -58,8 +58,9 @@ constexpr int kXCap = 1792;    // cells a CTA holds in shared memory (28 kB)
 
 // Host: the x-table parameters of ring pair (r, q); A2, B2 are the ring-pair
 // constants scaled to table-position units, lq the input ring's length, hw the
-// window half-width (whole-ring windows get no table).
-XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq);
+// window half-width (whole-ring windows get no table); scale <= 1 narrows the
+// cells of a table coarser than the automatic size (n_int / n_auto).
+XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq, double scale);
 
 // ---------------------------------------------------------------------------
 // Host FP64 split fit (Sec. 2, Eq. 1-6).

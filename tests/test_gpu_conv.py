@@ -69,6 +69,7 @@ def test_table_matches_oracle_legendre_sum(K):
     assert np.abs(lib - exact).max() <= 3e-7 * peak
 
 
+@pytest.mark.parametrize("exact_weights", [0, 1])
 @pytest.mark.parametrize("nside,tc_deg,lmax,fwhm_deg", [
     (1, 60.0, 3, 40.0),      # twelve pixels, several per disc
     (8, 180.0, 23, 10.0),    # whole sphere: every input ring, full-ring windows
@@ -76,11 +77,13 @@ def test_table_matches_oracle_legendre_sum(K):
     (32, 0.5, 95, 3.0),      # disc smaller than a pixel: only the self pair
     (64, 6.0, 191, 2.0),     # the 2-degree nside-64 workload (3 x FWHM cut)
 ])
-def test_full_map_parity(K, nside, tc_deg, lmax, fwhm_deg):
+def test_full_map_parity(K, nside, tc_deg, lmax, fwhm_deg, exact_weights):
+    """Both weight paths of the cap gather: dphi tables (default) and the exact
+    double-float chord for every pair."""
     tc = np.radians(tc_deg)
     c = inputs.gaussian_beam(lmax, np.radians(fwhm_deg))
     m = inputs.white_noise_map(nside, inputs.seed_for(1, nside)).astype(np.float32)
-    with K.make_split_real(c, nside, tc) as sp:
+    with K.make_split_real(c, nside, tc, exact_weights=exact_weights) as sp:
         n_int = K.split_info(sp)["n_intervals"]
         got = _run(K, sp, m)
     ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int))
@@ -88,6 +91,27 @@ def test_full_map_parity(K, nside, tc_deg, lmax, fwhm_deg):
     # against the exact kernel too (table interpolation error included)
     ex, amb2 = O.brute_conv(nside, m.astype(np.float64), tc, c=c)
     _check(got, ex, amb2, rel=2e-6)
+
+
+@pytest.mark.parametrize("nside,lmax,lcut,tc_deg,fwhm_deg", [
+    (128, 383, 64, 4.0, 1.0),    # oscillating high-pass remainder, caps of 127 rings
+    (256, 767, 192, 2.0, 0.5),   # longer rings: table cells stretched to fit
+])
+def test_dphi_tables_match_exact_weights(K, nside, lmax, lcut, tc_deg, fwhm_deg):
+    """The cap gather's dphi weight tables against exact per-pair weights: the tables'
+    interpolation error (at most 3e-7 of the kernel's peak per weight, rms ~1e-8) leaves
+    the two paths within the per-pixel parity tolerance (1e-6 of the output rms) of each
+    other; what remains is mostly the FP32 rounding of the largest outputs (a few ulp)."""
+    tc = np.radians(tc_deg)
+    c = inputs.gaussian_beam(lmax, np.radians(fwhm_deg))
+    c[: lcut + 1] = 0.0
+    m = inputs.white_noise_map(nside, inputs.seed_for(1, 1000 + nside)).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as a, K.make_split_real(c, nside, tc,
+                                                                 exact_weights=1) as b:
+        ya, yb = _run(K, a, m), _run(K, b, m)
+    rms = np.sqrt(np.mean(yb ** 2))
+    assert np.abs(ya - yb).max() <= 1e-6 * rms
+    assert np.sqrt(np.mean((ya - yb) ** 2)) <= 1e-7 * rms
 
 
 def test_self_pair_only(K):
