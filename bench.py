@@ -44,7 +44,7 @@ N_SM = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
 # capture of the current kernel (profiles/conv_sym_nside2048_dram.md)
-DRAM_TRAFFIC = {"conv_sym_kernel": 117.99e6 + 51.58e6}
+DRAM_TRAFFIC = {"conv_sym_kernel": 207.50e6 + 69.78e6}
 
 
 def workload_desc(extra=None):
