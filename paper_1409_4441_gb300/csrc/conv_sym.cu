@@ -155,29 +155,6 @@ __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, 
     for (int i = 0; i < NI; ++i) kahan(&sum[i], &comp[i], part[i]);
 }
 
-// The x table of ring pair g in shared memory: cell j holds the cubic
-// coefficients (in the cell offset) from the weights and slopes at boundaries j
-// and j + 1.  Each thread fills a run of consecutive cells, so every boundary
-// but the run's first is evaluated once.
-template <class S>
-__device__ __forceinline__ void build_xtab(const ConvPlan &P, const SymRing &g, float4 *xt) {
-    // an odd run length keeps the 16-byte stores of a warp on distinct banks
-    const int per = ((g.ncell + S::T - 1) / S::T) | 1;
-    const int j0 = threadIdx.x * per, j1 = min(j0 + per, g.ncell);
-    if (j0 >= j1) return;
-    float w0, d0;
-    xtab_node(P, g, j0, &w0, &d0);
-    for (int j = j0; j < j1; ++j) {
-        float w1, d1;
-        xtab_node(P, g, j + 1, &w1, &d1);
-        const float dw = w1 - w0;
-        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
-                            fmaf(-2.0f, dw, d0 + d1));
-        w0 = w1;
-        d0 = d1;
-    }
-}
-
 template <class S, bool MIRROR>
 __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n_cls,
                                          bool skip_belt_inputs, bool add, int band_lo,
@@ -217,7 +194,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             const bool use_xt = S::kXCap > 0 && g.ncell > 0 && g.ncell <= S::kXCap;
             if (use_xt) {  // (the segment's first barrier publishes the table)
                 __syncthreads();  // the previous ring pair's lookups are done
-                build_xtab<S>(P, g, xt);
+                xtab_build<S::T>(P, g, xt);
             }
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 // positions this segment needs (the union ends at U1)

@@ -96,25 +96,6 @@ __device__ __forceinline__ void build_a(const ConvPlan &P, const SymRing &g, con
     }
 }
 
-// The ring pair's x table (cubic coefficients per cell), all threads of the CTA
-// filling runs of consecutive cells (odd run length: distinct banks).
-__device__ __forceinline__ void build_xtab_mma(const ConvPlan &P, const SymRing &g, float4 *xt) {
-    const int per = ((g.ncell + kThreads - 1) / kThreads) | 1;
-    const int j0 = threadIdx.x * per, j1 = min(j0 + per, g.ncell);
-    if (j0 >= j1) return;
-    float w0, d0;
-    xtab_node(P, g, j0, &w0, &d0);
-    for (int j = j0; j < j1; ++j) {
-        float w1, d1;
-        xtab_node(P, g, j + 1, &w1, &d1);
-        const float dw = w1 - w0;
-        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
-                            fmaf(-2.0f, dw, d0 + d1));
-        w0 = w1;
-        d0 = d1;
-    }
-}
-
 // This lane's 8 B-tile values (two rows, four positions) of the tile starting
 // at pbase (see the assignment in the kernel).
 __device__ __forceinline__ void load_b(const float *const *src, int qoff, const bool *live,
@@ -226,7 +207,7 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 }
                 const bool use_xt = g.ncell > 0 && g.ncell <= kXCap;
                 if (use_xt) {  // (the previous ring pair ended at a barrier)
-                    build_xtab_mma(P, g, xt);
+                    xtab_build<kThreads>(P, g, xt);
                     __syncthreads();
                 }
                 const int P0 = U0 & ~(kKT - 1);

@@ -125,6 +125,29 @@ __device__ __forceinline__ void xtab_node(const ConvPlan &P, const SymRing &g, i
     *d = dk * dudx * g.dx.h;
 }
 
+// The ring pair's x table in shared memory, built by the T threads of a CTA:
+// cell j holds the cubic coefficients (in the cell offset) from the weights and
+// slopes at boundaries j and j + 1.  Each thread fills a run of consecutive
+// cells (every boundary but the run's first evaluated once; an odd run length
+// keeps a warp's 16-byte stores on distinct banks).
+template <int T>
+__device__ __forceinline__ void xtab_build(const ConvPlan &P, const SymRing &g, float4 *xt) {
+    const int per = ((g.ncell + T - 1) / T) | 1;
+    const int j0 = threadIdx.x * per, j1 = min(j0 + per, g.ncell);
+    if (j0 >= j1) return;
+    float w0, d0;
+    xtab_node(P, g, j0, &w0, &d0);
+    for (int j = j0; j < j1; ++j) {
+        float w1, d1;
+        xtab_node(P, g, j + 1, &w1, &d1);
+        const float dw = w1 - w0;
+        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
+                            fmaf(-2.0f, dw, d0 + d1));
+        w0 = w1;
+        d0 = d1;
+    }
+}
+
 // Weight of the pixel pair with exact integer Nf from the x table xt (cubic
 // coefficients per cell); zero beyond the cut.
 __device__ __forceinline__ float xtab_weight(const float4 *xt, const SymRing &g, float Nf) {
