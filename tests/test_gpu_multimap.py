@@ -56,3 +56,45 @@ def test_tensor_multimap_matches_ffma_and_oracle(K, nside, n_maps, tc_deg, lmax,
     ref, amb = O.brute_conv(nside, maps[j].astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int))
     rms_j = np.sqrt(np.mean(ref ** 2))
     assert np.all(np.abs(yt[j] - ref) <= 2e-6 * rms_j + amb)
+
+
+def test_tensor_stack_realistic_split_cl_error(K):
+    """A realistic map stack (16 maps at nside 512, 30' beam, least-squares split at
+    l_cut 384, theta_cut 960'): the tensor path's TF32 products and tensor-core FP32
+    accumulation stay at the C_l level the method targets.  Per pixel the tensor path
+    departs from the FFMA path by up to ~1e-5 of the output rms (rms ~1e-6): the
+    accumulator loses about one FP32 rounding per MMA step of a ring pair's partial sum,
+    so the deviation grows with the ring pairs' windows (1.5e-6 at nside 64, 1e-5 at
+    nside 512-2048).  The fractional rms C_l error between the two (Sec. 3's measure)
+    stays inside the 1e-5 target."""
+    ARC = inputs.ARCMIN
+    nside, lmax, lcut, tc = 512, 1535, 384, 960.0 * ARC
+    b = inputs.gaussian_beam(lmax, 30.0 * ARC)
+    cl = inputs.cl_grf(lmax)
+    n_maps = 16
+    maps = np.stack([inputs.white_noise_map(nside, 800 + i) for i in range(n_maps)]).astype(np.float32)
+    x = torch.tensor(maps, device="cuda")
+    with K.make_split(b, nside, lcut, tc, cl_in=cl) as sp, \
+            K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=1) as sf:
+        yt = torch.empty_like(x)
+        K.conv_real_multimap(sp, x, yt, n_maps)
+        yf = torch.empty_like(x)
+        K.conv_real_multimap(sf, x, yf, n_maps)
+        K.device_status(sp)
+        K.device_status(sf)
+    yt = yt.cpu().numpy().astype(np.float64)
+    yf = yf.cpu().numpy().astype(np.float64)
+    rms = np.sqrt(np.mean(yf ** 2))
+    d = yt - yf
+    print(f"\nnside 512 stack: max |tensor - ffma| / rms = {np.abs(d).max() / rms:.2e}, "
+          f"rms {np.sqrt(np.mean(d ** 2)) / rms:.2e}")
+    assert np.abs(d).max() <= 3e-5 * rms
+    assert np.sqrt(np.mean(d ** 2)) <= 2e-6 * rms
+    j = n_maps - 1
+    ct = O.alm2cl(O.map2alm(nside, yt[j], lmax), lmax)
+    cf = O.alm2cl(O.map2alm(nside, yf[j], lmax), lmax)
+    eps = O.eps_cl(ct, cf, lmin=2)
+    print(f"nside 512 stack: eps_C(tensor vs ffma) = {eps:.2e}")
+    # C^t - C^f ~ 2 <a^f a^d> + |a^d|^2: at most 2 x (rms of d / rms) = 4e-6 by the bound
+    # above, inside Sec. 3's 1e-5 target
+    assert eps <= 4e-6
