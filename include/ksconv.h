@@ -75,8 +75,10 @@ typedef struct {
                           1: general ring-pair gather only (reference path)   */
     int tensor;        /* map stacks (ksc_conv_real_multimap, n_maps >= 16):
                           0 (default): the symmetric (cap) ring pairs on the
-                          tcgen05 tensor cores (TF32 x3, FP32 accumulate),
-                          the belt ring pairs on the FFMA circulant kernel;
+                          tcgen05 tensor cores (TF32 x3, FP32 accumulate:
+                          per pixel within ~1e-5 of the output rms of the
+                          FFMA result, fractional rms C_l ~1e-6), the belt
+                          ring pairs on the FFMA circulant kernel;
                           1: FFMA kernels only; 2: both kinds of ring pair on
                           the tensor cores (the belt's tensor form is slower
                           than its circulant FFMA form on GB300)            */
