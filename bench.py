@@ -351,6 +351,7 @@ def run_ours(args, world, rank, local):
                                            "1/(l+10)^2, real-space part vanishing with zero "
                                            "slope at theta_cut"),
                                  "split_fit_s": round(t_split, 2),
+                                 "cap_weights_from_dphi_tables": round(info["frac_tabulated"], 4),
                                  "eq6_frac_error_alpha5": info["frac_error"],
                                  "parallelism": f"independent maps x{world}"}),
         "maps_per_s": world * args.steps / elapsed,

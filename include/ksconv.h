@@ -144,6 +144,10 @@ typedef struct {
     long long n_pairs;    /* ordered in-disc pixel pairs (one map), or -1     */
     long long n_pairs_belt; /* of which both pixels lie in the belt, or -1    */
     int path;             /* kernel path in use (see ksc_split_opts.path)     */
+    double frac_tabulated; /* share of the symmetric gather's weight
+                              evaluations (window positions x reflection
+                              classes) served by dphi tables (0 with
+                              exact_weights = 1)                              */
 } ksc_split_desc;
 
 /* Describe a split (host struct, filled synchronously). */

@@ -228,6 +228,27 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         }
     }
 
+    // Share of the symmetric gather's weight evaluations that the dphi tables serve
+    // (per northern output ring: reflection classes x window positions per input ring).
+    {
+        const int eqr = (nr - 1) / 2;
+        double all = 0.0, tab = 0.0;
+        for (int r = 0; r <= eqr; ++r) {
+            const bool belt_r = r >= belt_lo && r <= belt_hi;
+            const double cls = (double)ksc::sym_classes(g.len[r], g.phase[r]);
+            for (int q = range[r].x; q <= range[r].y; ++q) {
+                const size_t ip = (size_t)pair_base[r] + (q - range[r].x);
+                if (pairs[ip].hw < 0.0f) continue;
+                const bool belt_q = q >= belt_lo && q <= belt_hi;
+                if (s->path == 0 && belt_r && belt_q && !items_belt.empty()) continue;
+                const double n = cls * std::min(2.0 * pairs[ip].hw + 3.0, (double)g.len[q]);
+                all += n;
+                if (xinfo[ip].ncell > 0) tab += n;
+            }
+        }
+        s->frac_tabulated = all > 0.0 ? tab / all : 0.0;
+    }
+
     // The symmetric items longest first, for whole-map launches: CTAs claim items
     // in list order, so the long items start first and the short ones fill the tail.
     std::vector<ksc::WorkItem> items_lpt(items_sym);
@@ -555,6 +576,7 @@ int ksc_split_info(const ksc_split *s, ksc_split_desc *d) {
     d->theta_cut = s->theta_cut; d->chord_cut = s->chord_cut;
     d->sigma_rms = s->sigma_rms; d->frac_error = s->frac_error; d->n_pairs = s->n_pairs;
     d->n_pairs_belt = s->n_pairs_belt; d->path = s->path;
+    d->frac_tabulated = s->frac_tabulated;
     return KSC_OK;
 }
 

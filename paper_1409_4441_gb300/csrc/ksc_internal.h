@@ -221,6 +221,7 @@ struct ksc_split {
     int2 *d_range = nullptr;
     ksc::PairInfo *d_pairs = nullptr;
     ksc::XInfo *d_xinfo = nullptr;
+    double frac_tabulated = 0.0;  // share of gather weights from dphi tables
     int *d_pair_base = nullptr;
     // work lists, each with a per-ring prefix (nrings + 1 offsets)
     ksc::WorkItem *d_items = nullptr;   // every ring (pair counting)

@@ -66,7 +66,7 @@ class Desc(ctypes.Structure):
                 ("theta_cut", ctypes.c_double), ("chord_cut", ctypes.c_double),
                 ("sigma_rms", ctypes.c_double), ("frac_error", ctypes.c_double),
                 ("n_pairs", ctypes.c_longlong), ("n_pairs_belt", ctypes.c_longlong),
-                ("path", ctypes.c_int)]
+                ("path", ctypes.c_int), ("frac_tabulated", ctypes.c_double)]
 
 
 class BatchOpts(ctypes.Structure):
