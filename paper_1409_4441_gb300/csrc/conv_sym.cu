@@ -19,12 +19,15 @@
 // threads' windows, the sixteen image sequences m[image(k')] in shared memory
 // so that every image of input position k' sits at the same offset; each
 // thread then walks its window four positions at a time: four independent
-// kernel evaluations, then one 16-byte shared load per image feeding four
-// FFMAs.  Chord and table position are computed in double-float from the
-// ring-pair table and the exact integer N = (2k + t) L' - (2k' + t') L,
-// dphi / 2 = N pi / (2 L L') (ksc_device.cuh); K_r comes from the cubic
-// Hermite table through the L1 cache.  FP32 partial sums over 32 positions are
-// Kahan-folded into the totals.
+// kernel weights, then one 16-byte shared load per image feeding four FFMAs.
+// A weight depends on the pixel pair only through the exact integer
+// N = (2k + t) L' - (2k' + t') L, dphi / 2 = N pi / (2 L L').  Per input ring
+// the CTA first builds the ring pair's weight table in dphi in shared memory
+// (cubic cells, each from the double-float chord and the K_r table at its two
+// ends, ksc_sym.cuh); a weight is then one cell lookup and three FMAs.  Ring
+// pairs without a table (whole-ring windows, or more cells than a CTA holds)
+// evaluate the double-float chord and the K_r table per pair (ksc_device.cuh).
+// FP32 partial sums over 32 positions are Kahan-folded into the totals.
 //
 // Paired lanes (tile variant 2): two adjacent lanes own one class.  Each
 // evaluates two of every four kernel weights, the pair swaps them with one
@@ -105,9 +108,9 @@ __device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing 
 }
 
 // Positions a..b of one staged segment (starting at s0) for one thread.  The
-// loop is software-pipelined: the weights of the next quad are evaluated
-// while the current quad's weights feed the FFMAs, so the long double-float
-// chains overlap the multiply-adds.
+// loop is software-pipelined: the weights of the next quad (table lookups, or
+// double-float chains) are evaluated while the current quad's weights feed the
+// FFMAs.
 template <class S, bool MIRROR, int MODE>
 __device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float4 *xt,
                                            const float *st, int s0, int a, int b, long long num,
