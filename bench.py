@@ -362,7 +362,9 @@ def run_ours(args, world, rank, local):
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + "
                                      "dram__bytes_write.sum, profiles/conv_sym_nside2048_dram.md)",
                      "note": "2 FLOP (one FMA) per in-disc pixel pair the kernel handles; "
-                             "peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock"},
+                             "peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock; the cap "
+                             "gather's limiter is shared-memory traffic (ncu: l1tex 76% of "
+                             "peak, profiles/conv_sym_dphi_tables_nside512_ncu.md)"},
         "stages": stages,
         "step_tflops": 2.0 * n_pairs / statistics.mean(launch_ms) * 1e3 / 1e12,
         "e2e": {"value": total_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 4 * npix,
