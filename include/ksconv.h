@@ -315,6 +315,21 @@ int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in,
 int ksc_count_pairs(ksc_split *s, long long *n_pairs);
 
 /*
+ * The dphi weight table the symmetric gather builds for one ring pair, as the
+ * library sizes it (host arithmetic only, no device work; for inspection).
+ * For output ring r (L pixels) and input ring q (lq pixels) the squared chord in
+ * K_r-table units is A2 + B2 sin^2 x, x = dphi / 2 = |N| c, c = pi / (2 L lq),
+ * n_int the table's intervals (the cut is A2 + B2 sin^2 x <= n_int^2); hw is
+ * the gather's window half-width in input pixels (< 0: no pair within the cut;
+ * 2 hw + 3 >= lq: the window is the whole ring, which gets no table), scale
+ * = min(1, n_int / automatic n_int).  out[0] = cell width in x (radians),
+ * out[1] = number of cells (0: per-pair chord weights), out[2] = the largest
+ * |N| within the cut.  KSC_ERR_ARG for a null out, c <= 0 or n_int < 1.
+ */
+int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw,
+                          int lq, double scale, double *out);
+
+/*
  * Synchronize `stream` and report device-side errors raised by earlier calls
  * on this split: KSC_ERR_TIMEOUT when a bounded wait inside a kernel ran out
  * (the kernel stopped early and its output is incomplete),

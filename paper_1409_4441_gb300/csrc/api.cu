@@ -467,7 +467,9 @@ XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq,
     }
     if (!(dmax > 0.0)) return x;
     const double dx = std::max(scale * kXRho / dmax, xcut / (kXCap - 2.0));
-    const double cells = std::floor(xcut / dx) + 2.0;  // in-cut positions stay below ncell - 1
+    // in-cut positions p = x / dx <= floor(xcut / dx) + 1 = ncell - 1: inside the last cell,
+    // below the device's clamp at ncell - 0.5
+    const double cells = std::floor(xcut / dx) + 2.0;
     if (cells > (double)kXCap || dx * dmax > scale * kXRhoMax || cells * dx > 0.5 * kPi + 0.05)
         return x;
     const DF dxd = df_from_double(dx), R = df_from_double(c / dx);
@@ -566,6 +568,17 @@ int ksc_make_split_real(const double *c_l, int lmax, int nside, double theta_cut
     rc = finish_split(s, o);
     if (rc) { release(s); return rc; }
     *out = s;
+    return KSC_OK;
+}
+
+int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw, int lq,
+                          double scale, double *out) {
+    if (!out || !(c > 0.0) || n_int < 1) return fail(KSC_ERR_ARG, "bad table parameters");
+    const ksc::XInfo x = ksc::make_xinfo(A2, B2, c, (double)n_int * (double)n_int, (float)hw,
+                                         lq, scale);
+    out[0] = (double)x.dxh + (double)x.dxl;
+    out[1] = (double)x.ncell;
+    out[2] = x.ncell > 0 ? (double)x.ncut : 0.0;
     return KSC_OK;
 }
 

@@ -40,7 +40,7 @@ EXPORTS = [
     "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
     "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
     "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_conv_real_multimap_stage",
-    "ksc_count_pairs", "ksc_device_status",
+    "ksc_count_pairs", "ksc_device_status", "ksc_dphi_table_params",
     "ksc_free_split", "ksc_build_table_noalloc",
     "ksc_batch_default_opts", "ksc_batch_create", "ksc_batch_run", "ksc_batch_autotune",
     "ksc_batch_info", "ksc_batch_status", "ksc_batch_free",
@@ -106,6 +106,7 @@ _sig = {
     "ksc_conv_real_stage": [_vp, _vp, _vp, _i, _vp],
     "ksc_conv_real_multimap_stage": [_vp, _vp, _vp, _i, _i, _vp],
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
+    "ksc_dphi_table_params": [_d, _d, _d, _i, _d, _i, _d, _vp],
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
     "ksc_build_table_noalloc": [_vp, _i, _d, _i, _vp, _vp],
@@ -272,6 +273,17 @@ def count_pairs(s: Split) -> int:
     n = ctypes.c_longlong()
     _check(_lib.ksc_count_pairs(s.handle, ctypes.byref(n)), "ksc_count_pairs")
     return n.value
+
+
+def dphi_table_params(A2: float, B2: float, c: float, n_int: int, hw: float, lq: int,
+                      scale: float = 1.0) -> dict:
+    """ksc_dphi_table_params: cell width (radians of x = dphi/2), cell count and the
+    cut in |N| of one ring pair's dphi weight table (host only)."""
+    out = np.zeros(3)
+    _check(_lib.ksc_dphi_table_params(float(A2), float(B2), float(c), int(n_int), float(hw),
+                                      int(lq), float(scale), out.ctypes.data),
+           "ksc_dphi_table_params")
+    return {"dx": float(out[0]), "ncell": int(out[1]), "ncut": float(out[2])}
 
 
 def device_status(s: Split, stream=None):
