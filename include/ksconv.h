@@ -166,7 +166,11 @@ int ksc_split_table(const ksc_split *s, float *host_coeffs);
 /*
  * out = real-space convolution of `in` with the split's K_r (both device
  * arrays of 12 nside^2 floats, nside as given to the split; in != out).
- * Asynchronous on `stream`.  Errors: KSC_ERR_ARG, KSC_ERR_CUDA.
+ * Asynchronous on `stream`.  Each call takes a few bytes of work-claim
+ * counters from the device's default stream-ordered memory pool
+ * (cudaMallocAsync / cudaFreeAsync on `stream`), so calls on several streams
+ * may overlap and a call captured into a CUDA graph holds its own counters.
+ * Errors: KSC_ERR_ARG, KSC_ERR_CUDA.
  */
 int ksc_conv_real(const ksc_split *s, const float *d_in, float *d_out,
                   void *stream);
