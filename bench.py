@@ -47,7 +47,7 @@ UNIT = "pairs/s"
 N_SM = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
-# capture of the current kernel (profiles/conv_sym_nside2048_dram.md)
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, full launch)
 DRAM_TRAFFIC = {"conv_sym_kernel": 207.50e6 + 69.78e6}
 
 

@@ -370,7 +370,7 @@ int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
  * fractional-rms C_l error of the split convolution and the GPU time of its
  * real-space part.  It stands beside the paper's Eq. 6 error estimate and
  * Eq. 7-8 cost models (Sec. 2 scan) so a split meeting an error bound can be
- * chosen without trial runs; a measured run remains the judge.  It is trained
+ * chosen without trial runs; a measured run remains the final check.  It is trained
  * on the GPU by the library's own forward / backward / Adam kernels (the paper
  * has no counterpart).  Parameters: one flat FP32 array of
  * ksc_mlp_n_params() values, W1[4][64] b1[64] W2[64][64] b2[64] W3[64][2] b3[2]
