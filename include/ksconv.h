@@ -343,6 +343,17 @@ int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw,
 int ksc_device_status(const ksc_split *s, void *stream);
 
 /*
+ * Exercise the bounded-wait failure path on `stream`: one CTA waits on a
+ * shared-memory mbarrier that no thread ever arrives on, with the same bounded
+ * poll loop as the tensor-core kernels; when the limit runs out (2^22 polls,
+ * about 16 s on a GB300) it raises this split's device error flag as a kernel
+ * would, and returns.  Nothing hangs or faults: the next ksc_device_status reports
+ * KSC_ERR_TIMEOUT and clears the flag, and the context stays usable.
+ * Asynchronous; errors: KSC_ERR_ARG, KSC_ERR_CUDA.
+ */
+int ksc_probe_wait_timeout(const ksc_split *s, void *stream);
+
+/*
  * Allocation-free table build (the paper has no counterpart: this serves
  * callers that cannot allocate device memory where they need a table, such as
  * code under a caching allocator or a fixed memory budget that owns all

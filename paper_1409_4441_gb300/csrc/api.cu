@@ -9,8 +9,22 @@
 
 #include "ksc_device.cuh"
 #include "ksc_internal.h"
+#include "ksc_tc.cuh"
 
 namespace {
+
+// One CTA waits on an mbarrier nothing arrives on (phase 0 never completes); the
+// bounded wait runs out and the CTA raises the error flag like a kernel would.
+__global__ void wait_probe_kernel(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        ksc::tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool done = ksc::tc::mbar_wait(&bar, 0u);
+    if (!done && threadIdx.x == 0) atomicExch(err, KSC_ERR_TIMEOUT);
+}
 
 thread_local std::string g_last_error;
 
@@ -702,6 +716,14 @@ int ksc_device_status(const ksc_split *s, void *stream) {
         cudaMemset(s->d_err, 0, sizeof(int));
         return fail(flag, "a device-side check fired during an earlier call");
     }
+    return KSC_OK;
+}
+
+int ksc_probe_wait_timeout(const ksc_split *s, void *stream) {
+    if (!s) return fail(KSC_ERR_ARG, "null split");
+    wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(s->d_err);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe launch");
     return KSC_OK;
 }
 

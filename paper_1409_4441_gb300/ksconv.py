@@ -40,7 +40,7 @@ EXPORTS = [
     "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
     "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
     "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_conv_real_multimap_stage",
-    "ksc_count_pairs", "ksc_device_status", "ksc_dphi_table_params",
+    "ksc_count_pairs", "ksc_device_status", "ksc_dphi_table_params", "ksc_probe_wait_timeout",
     "ksc_free_split", "ksc_build_table_noalloc",
     "ksc_batch_default_opts", "ksc_batch_create", "ksc_batch_run", "ksc_batch_autotune",
     "ksc_batch_info", "ksc_batch_status", "ksc_batch_free",
@@ -107,6 +107,7 @@ _sig = {
     "ksc_conv_real_multimap_stage": [_vp, _vp, _vp, _i, _i, _vp],
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
     "ksc_dphi_table_params": [_d, _d, _d, _i, _d, _i, _d, _vp],
+    "ksc_probe_wait_timeout": [_vp, _vp],
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
     "ksc_build_table_noalloc": [_vp, _i, _d, _i, _vp, _vp],
@@ -284,6 +285,12 @@ def dphi_table_params(A2: float, B2: float, c: float, n_int: int, hw: float, lq:
                                       int(lq), float(scale), out.ctypes.data),
            "ksc_dphi_table_params")
     return {"dx": float(out[0]), "ncell": int(out[1]), "ncut": float(out[2])}
+
+
+def probe_wait_timeout(s: Split, stream=None):
+    """Run one bounded wait that nothing completes; the next device_status raises
+    KSC_ERR_TIMEOUT (and clears it)."""
+    _check(_lib.ksc_probe_wait_timeout(s.handle, _stream(stream)), "ksc_probe_wait_timeout")
 
 
 def device_status(s: Split, stream=None):

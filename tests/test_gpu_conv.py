@@ -264,3 +264,25 @@ def test_stages_compose_bitwise_and_counts(K):
     assert 0 < info["n_pairs_belt"] < n
     assert abs(info["n_pairs_belt"] - O.count_pairs(nside, tc, out_pix=np.where(belt)[0]).sum()) \
         <= abs(n - info["n_pairs_belt"])  # sanity: belt outputs dominate belt-belt pairs
+
+
+def test_bounded_wait_runs_out_and_context_survives(K):
+    """Failure detection without a fault: a bounded mbarrier wait that nothing
+    completes runs out, the CTA raises the split's device error flag and returns; the
+    host reads KSC_ERR_TIMEOUT once (the flag is cleared), and the same context then
+    convolves a map within the oracle parity."""
+    nside = 16
+    tc = np.radians(20.0)
+    c = inputs.gaussian_beam(47, np.radians(6.0))
+    m = inputs.white_noise_map(nside, 77).astype(np.float32)
+    with K.make_split_real(c, nside, tc) as sp:
+        K.probe_wait_timeout(sp)
+        with pytest.raises(K.KsconvError) as e:
+            K.device_status(sp)
+        assert e.value.code == K.KSC_ERR_TIMEOUT
+        K.device_status(sp)  # cleared
+        n_int = K.split_info(sp)["n_intervals"]
+        got = _run(K, sp, m)
+        K.device_status(sp)
+    ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int))
+    _check(got, ref, amb)
