@@ -47,8 +47,9 @@ UNIT = "pairs/s"
 N_SM = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
-# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, full launch)
-DRAM_TRAFFIC = {"conv_sym_kernel": 207.50e6 + 69.78e6}
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, full launch);
+# absent until the current kernel has been captured
+DRAM_TRAFFIC = {}
 
 
 def workload_desc(extra=None):
@@ -212,9 +213,9 @@ def run_ours(args, world, rank, local):
     cl = inputs.cl_grf(lmax)
     t0 = time.perf_counter()
     if lcut is None:  # no split: the whole beam in real space
-        sp = K.make_split_real(b, nside, tc)
+        sp = K.make_split_real(b, nside, tc, **split_opts(args))
     else:
-        sp = K.make_split(b, nside, lcut, tc, cl_in=cl)
+        sp = K.make_split(b, nside, lcut, tc, cl_in=cl, **split_opts(args))
     t_split = time.perf_counter() - t0
     flush = None
     if npix * 4 <= 129e6:  # map smaller than L2: flush it between timed steps
@@ -360,11 +361,13 @@ def run_ours(args, world, rank, local):
                      "frac": achieved / peak_tflops,
                      "traffic": DRAM_TRAFFIC.get(dom) if args.workload == "nside2048" else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + "
-                                     "dram__bytes_write.sum, profiles/conv_sym_nside2048_dram.md)",
+                                     "dram__bytes_write.sum of one full-size launch)",
                      "note": "2 FLOP (one FMA) per in-disc pixel pair the kernel handles; "
                              "peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock; the cap "
-                             "gather's limiter is shared-memory traffic (ncu: l1tex 76% of "
-                             "peak, profiles/conv_sym_dphi_tables_nside512_ncu.md)"},
+                             "gather is bound by shared-memory bandwidth to the lanes "
+                             "(ncu l1tex__throughput, l1tex__data_bank_conflicts_pipe_lsu_"
+                             "mem_shared_op_ld: its weight-cell loads are random across "
+                             "lanes)"},
         "stages": stages,
         "step_tflops": 2.0 * n_pairs / statistics.mean(launch_ms) * 1e3 / 1e12,
         "e2e": {"value": total_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 4 * npix,
@@ -377,6 +380,32 @@ def run_ours(args, world, rank, local):
         "batch": batch,
     }
     print(json.dumps(line), flush=True)
+    sp.close()
+
+
+def split_opts(args):
+    """Split options chosen on the command line (the library's defaults otherwise)."""
+    return {} if args.cap_kernel is None else {"cap_kernel": args.cap_kernel}
+
+
+def run_band(args):
+    """Profiling case: output rings lo..hi of the benchmark workload (a band of
+    cap rings, so that ncu can capture the cap gather's per-ring-pair shapes at
+    nside 2048 in a launch of tens of ms).  Prints the band's launch time."""
+    import torch
+    from paper_1409_4441_gb300 import ksconv as K
+    dev = torch.device("cuda", 0)
+    lo, hi = args.band
+    nside, lmax, lcut, tc = (WORKLOAD[k] for k in ("nside", "lmax", "lcut", "theta_cut"))
+    b = inputs.gaussian_beam(lmax, WORKLOAD["fwhm"])
+    sp = K.make_split(b, nside, lcut, tc, cl_in=inputs.cl_grf(lmax), **split_opts(args))
+    m = inputs.white_noise_map(nside, inputs.seed_for(3)).astype(np.float32)
+    x = torch.tensor(m, device=dev)
+    y = torch.zeros_like(x)
+    ms = _event_ms(lambda: K.conv_real_rings(sp, x, y, lo, hi), torch.cuda.current_stream(),
+                   torch, reps=args.steps)
+    K.device_status(sp)
+    print(json.dumps({"band": [lo, hi], "ms": ms, "workload": workload_desc()}), flush=True)
     sp.close()
 
 
@@ -582,10 +611,17 @@ def main():
     ap.add_argument("--mm-nside", type=int, default=1024)
     ap.add_argument("--mm-maps", type=int, default=64)
     ap.add_argument("--workload", default="nside2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--cap-kernel", type=int, choices=[0, 1], default=None,
+                    help="ksc_split_opts.cap_kernel for the timed split (default: library's)")
+    ap.add_argument("--band", type=int, nargs=2, metavar=("LO", "HI"),
+                    help="profiling case: only output rings LO..HI (1-based), timed alone")
     args = ap.parse_args()
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
     world, rank, local = dist_setup()
+    if args.band and args.impl != "reference":
+        run_band(args)
+        return
     if args.multimap_only and args.impl != "reference":
         import torch
         from paper_1409_4441_gb300 import ksconv as K

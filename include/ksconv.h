@@ -96,6 +96,18 @@ typedef struct {
                           at most 3e-7 of the kernel's peak, rms about 1e-8);
                           1: every weight from the double-float chord and
                           the K_r table                                      */
+    int cap_kernel;    /* single maps and stacks of fewer than 16 maps: which
+                          kernel sums the cap ring pairs.  0 (default): FP32
+                          FFMAs, three reflection classes per thread sharing
+                          each staged image value; 1: the tcgen05 tensor
+                          cores, each weight and map value split exactly into
+                          three BF16 parts and six MMAs per 16 positions
+                          (products to FP32 rounding), a fresh accumulator
+                          drained every 16 positions into Kahan-folded FP32
+                          sums (slower for one map: each weight serves only
+                          the 16 symmetry images).  Both use the same
+                          weights; their outputs agree to FP32 rounding of
+                          the sums                                          */
 } ksc_split_opts;
 
 #define KSC_CUT_C1 0
@@ -256,8 +268,10 @@ typedef struct {
     int n_groups;              /* nside groups tuned (at most 8 reported)    */
     int nside[8];
     int belt_variant[8];       /* 0: 2080-output belt items, 1: 1040         */
-    int sym_variant[8];        /* 0: 128-class gather items, 1: 64, 2: 64
-                                  classes on paired lanes (128 threads)      */
+    int sym_variant[8];        /* gather items: 0: 256 classes (4096-cell
+                                  weight tables, 2 CTAs per SM), 1: 128
+                                  classes (2048 cells, 3 CTAs per SM), 2: 128
+                                  classes (4096 cells, 2 CTAs per SM)        */
     double ms_belt[8][2];      /* median launch time of each belt variant    */
     double ms_sym[8][3];       /* median launch time of each gather variant  */
 } ksc_tune_report;

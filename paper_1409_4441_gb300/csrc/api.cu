@@ -62,6 +62,8 @@ void release(ksc_split *s) {
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
     cudaFree(s->d_items_sym_lpt);
+    cudaFree(s->d_items_smma);
+    cudaFree(s->d_items_smma_lpt);
     cudaFree(s->d_items_mma);
     cudaFree(s->d_ws);
     cudaFree(s->d_items_belt);
@@ -130,7 +132,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         const bool belt = r >= belt_lo && r <= belt_hi;
         const bool reaches_cap = range[r].x < belt_lo || range[r].y > belt_hi;
         if (r <= eq && (!belt || reaches_cap || o.path == 1))
-            for (int k0 = 0; k0 < ksc::sym_classes(g.len[r], g.phase[r]); k0 += ksc::sym_chunk())
+            for (int k0 = 0; k0 < ksc::sym_classes(g.len[r], g.phase[r]);
+                 k0 += ksc::sym_chunk(nside))
                 items_sym.push_back({r, k0});
         if (belt) {
             for (int k0 = 0; k0 < g.len[r]; k0 += bc) items_belt.push_back(make_int2(r, k0));
@@ -221,7 +224,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                         ? ksc::XInfo{}
                         : ksc::make_xinfo(A * scale2, 4.0 * ss * scale2,
                                           kPi / (2.0 * (double)g.len[r] * (double)Lq),
-                                          (double)n_int * (double)n_int, pi.hw, Lq, xscale);
+                                          (double)n_int * (double)n_int, pi.hw, g.len[r], Lq,
+                                          xscale);
             }
         }
     }
@@ -265,18 +269,39 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
 
     // The symmetric items longest first, for whole-map launches: CTAs claim items
     // in list order, so the long items start first and the short ones fill the tail.
-    std::vector<ksc::WorkItem> items_lpt(items_sym);
-    {
+    // The tensor cap kernel has items of its own size.
+    auto lpt = [&](std::vector<ksc::WorkItem> v, int chunk) {
         auto cost = [&](const ksc::WorkItem &w) {
             const int n_cls = ksc::sym_classes(g.len[w.ring], g.phase[w.ring]);
-            const int cnt = std::min(ksc::sym_chunk(), n_cls - w.k0);
+            const int cnt = std::min(chunk, n_cls - w.k0);
             return cnt * s->cost_sym[w.ring] * (w.ring == eq ? 1.0 : 2.0);
         };
-        std::stable_sort(items_lpt.begin(), items_lpt.end(),
-                         [&](const ksc::WorkItem &x, const ksc::WorkItem &y) {
-                             return cost(x) > cost(y);
-                         });
+        std::stable_sort(v.begin(), v.end(), [&](const ksc::WorkItem &x, const ksc::WorkItem &y) {
+            return cost(x) > cost(y);
+        });
+        return v;
+    };
+    std::vector<ksc::WorkItem> items_lpt = lpt(items_sym, ksc::sym_chunk(nside));
+    // 128-class items of the tensor kernels, ring by ring (with per-ring prefixes
+    // for latitude bands) and longest first
+    std::vector<ksc::WorkItem> items_smma;
+    s->ring_first_smma.assign(nr + 1, 0);
+    {
+        size_t i = 0;
+        for (int r = 0; r < nr; ++r) {
+            s->ring_first_smma[r] = (int)items_smma.size();
+            if (i < items_sym.size() && items_sym[i].ring == r) {
+                const int n_cls = ksc::sym_classes(g.len[r], g.phase[r]);
+                for (int k0 = 0; k0 < n_cls; k0 += ksc::sym_mma_chunk())
+                    items_smma.push_back({r, k0});
+                while (i < items_sym.size() && items_sym[i].ring == r) ++i;
+            }
+        }
+        s->ring_first_smma[nr] = (int)items_smma.size();
     }
+    std::vector<ksc::WorkItem> items_smma_lpt = lpt(items_smma, ksc::sym_mma_chunk());
+    s->n_items_smma = (int)items_smma.size();
+    s->cap_kernel = o.cap_kernel;
 
     cudaError_t e;
     cudaGetDevice(&s->device);
@@ -295,6 +320,11 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     if ((e = dev_upload(&s->d_items_sym, items_sym.data(), items_sym.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
     if ((e = dev_upload(&s->d_items_sym_lpt, items_lpt.data(), items_lpt.size())) != cudaSuccess)
+        return cuda_fail(e, "upload work list");
+    if ((e = dev_upload(&s->d_items_smma, items_smma.data(), items_smma.size())) != cudaSuccess)
+        return cuda_fail(e, "upload work list");
+    if ((e = dev_upload(&s->d_items_smma_lpt, items_smma_lpt.data(), items_smma_lpt.size())) !=
+        cudaSuccess)
         return cuda_fail(e, "upload work list");
     if ((e = dev_upload(&s->d_items_belt, items_belt.data(), items_belt.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
@@ -376,6 +406,7 @@ ksc_split_opts resolve_opts(const ksc_split_opts *opts) {
         if (o.cut_continuity < KSC_CUT_C1 || o.cut_continuity > KSC_CUT_FREE)
             o.cut_continuity = KSC_CUT_C1;
         if (o.exact_weights != 1) o.exact_weights = 0;
+        if (o.cap_kernel != 1) o.cap_kernel = 0;
     }
     return o;
 }
@@ -411,6 +442,30 @@ int launch_belt_tensor(const ksc_split *cs, const float *d_in, float *d_out, int
     return KSC_OK;
 }
 
+// The cap stage for the items of northern rings [lo, hi], writing output rings
+// [r0, r1]: the map-stack tensor kernel for whole-map stacks, else the FFMA gather
+// or the single-map tensor kernel (ksc_split_opts.cap_kernel).  Whole maps take
+// the items longest first, bands their rings' items in ring order.
+cudaError_t launch_caps(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
+                        long long stride, int lo, int hi, int r0, int r1, bool stack,
+                        cudaStream_t st) {
+    const bool whole = r0 == 0 && r1 == s->plan.nrings - 1;
+    const int belt_split = s->n_items_belt > 0 ? 1 : 0;
+    if (stack && s->tensor != 1)
+        return ksc::launch_conv_sym_mma(s->plan, s->d_items_smma_lpt, s->n_items_smma, d_in,
+                                        d_out, n_maps, stride, belt_split, s->d_err, st);
+    if (s->cap_kernel == 1) {
+        const int c = s->ring_first_smma[lo], d = s->ring_first_smma[hi + 1];
+        const ksc::WorkItem *its = whole ? s->d_items_smma_lpt : s->d_items_smma + c;
+        return ksc::launch_conv_sym_tc(s->plan, its, d - c, d_in, d_out, n_maps, stride,
+                                       belt_split, r0, r1, s->d_err, st);
+    }
+    const int c = s->ring_first_sym[lo], d = s->ring_first_sym[hi + 1];
+    const ksc::WorkItem *its = whole ? s->d_items_sym_lpt : s->d_items_sym + c;
+    return ksc::launch_conv_sym(s->plan, its, d - c, d_in, d_out, n_maps, stride, belt_split,
+                                r0, r1, st);
+}
+
 // The real-space convolution of output rings [r0, r1] (0-based, inclusive).
 // Default path: circulant belt kernel first (writes belt outputs), then the
 // symmetric gather (writes cap outputs, adds cap inputs to belt outputs).
@@ -443,15 +498,7 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
     const int m0 = std::max(0, nr - 1 - r1), m1 = std::min(nr - 1 - r0, eq);
     if (m0 <= m1) { lo = std::min(lo, m0); hi = std::max(hi, m1); }  // mirror in band
     if (lo <= hi) {
-        const int c = s->ring_first_sym[lo], d = s->ring_first_sym[hi + 1];
-        // whole map: the items longest first; a band: its rings' items
-        const ksc::WorkItem *its = whole ? s->d_items_sym_lpt : s->d_items_sym + c;
-        if (stack && s->tensor != 1)
-            e = ksc::launch_conv_sym_mma(s->plan, its, d - c, d_in, d_out, n_maps, stride,
-                                         s->n_items_belt > 0 ? 1 : 0, s->d_err, st);
-        else
-            e = ksc::launch_conv_sym(s->plan, its, d - c, d_in, d_out, n_maps, stride,
-                                     s->n_items_belt > 0 ? 1 : 0, r0, r1, st);
+        e = launch_caps(s, d_in, d_out, n_maps, stride, lo, hi, r0, r1, stack, st);
         if (e != cudaSuccess) return cuda_fail(e, "symmetric kernel launch");
     }
     return KSC_OK;
@@ -462,7 +509,8 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
 namespace ksc {
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 
-XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq, double scale) {
+XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int L, int lq,
+                 double scale) {
     XInfo x{};
     // no pair within the cut, or a whole-ring window: no table
     if (hw < 0.0f || 2.0f * hw + 3.0f >= (float)lq || A2 >= nint2 || B2 <= 0.0) return x;
@@ -480,20 +528,27 @@ XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq,
         dmax = B2 * std::sqrt(S * (1.0 - S) / (A2 + B2 * S));
     }
     if (!(dmax > 0.0)) return x;
-    const double dx = std::max(scale * kXRho / dmax, xcut / (kXCap - 2.0));
-    // in-cut positions p = x / dx <= floor(xcut / dx) + 1 = ncell - 1: inside the last cell,
-    // below the device's clamp at ncell - 0.5
-    const double cells = std::floor(xcut / dx) + 2.0;
-    if (cells > (double)kXCap || dx * dmax > scale * kXRhoMax || cells * dx > 0.5 * kPi + 0.05)
-        return x;
-    const DF dxd = df_from_double(dx), R = df_from_double(c / dx);
-    x.dxh = dxd.h;
-    x.dxl = dxd.l;
-    x.Rh = R.h;
-    x.Rl = R.l;
-    x.ncut = (float)std::floor(xcut / c);
-    x.ncell = (int)cells;
-    x.pmax = (float)cells - 0.5f;
+    // the largest |N| within the cut: |N| c <= xcut
+    const double nc = std::floor(xcut / c);
+    if (nc >= 8388608.0) return x;  // |N| and the quads' reach stay below 2^24
+    const int ncut = (int)nc;
+    // widest power-of-two cell within kXRho intervals at the steepest point, and no
+    // wider than the in-cut range (so that no node lies more than one cell beyond the
+    // cut, where the K_r table is extrapolated) ...
+    int shift = (int)std::floor(std::log2(scale * kXRho / (dmax * c)));
+    shift = std::max(shift, 0);
+    while (shift > 0 && std::ldexp(c, shift) * dmax > scale * kXRho) --shift;  // log2 rounding
+    while (shift > 0 && (1 << std::min(shift, 30)) > ncut + 1) --shift;
+    // ... doubled while the cells (and the reach of an edge quad) would not fit
+    auto cells = [&](int sh) { return (ncut >> sh) + 1; };
+    while (cells(shift) + kXPad(L, shift) > kXCap && shift < 22) ++shift;
+    if (cells(shift) + kXPad(L, shift) > kXCap) return x;
+    if (std::ldexp(c, shift) * dmax > scale * kXRhoMax * (1.0 + 1e-12) && shift > 0) return x;
+    // integers of in-cut pairs and of positions up to 16 beyond them stay exact in FP32
+    if ((double)ncut + 32.0 * (double)L + std::ldexp(1.0, shift) >= 16777216.0) return x;
+    x.shift = shift;
+    x.ncut = ncut;
+    x.ncell = cells(shift);
     return x;
 }
 } // namespace ksc
@@ -511,6 +566,7 @@ int ksc_default_opts(ksc_split_opts *opts) {
     opts->tensor = 0;
     opts->cut_continuity = KSC_CUT_C1;
     opts->exact_weights = 0;
+    opts->cap_kernel = 0;
     return KSC_OK;
 }
 
@@ -588,9 +644,11 @@ int ksc_make_split_real(const double *c_l, int lmax, int nside, double theta_cut
 int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw, int lq,
                           double scale, double *out) {
     if (!out || !(c > 0.0) || n_int < 1) return fail(KSC_ERR_ARG, "bad table parameters");
+    // the output ring's length from c = pi / (2 L lq)
+    const int L = lq > 0 ? (int)std::lround(kPi / (2.0 * c * (double)lq)) : 1;
     const ksc::XInfo x = ksc::make_xinfo(A2, B2, c, (double)n_int * (double)n_int, (float)hw,
-                                         lq, scale);
-    out[0] = (double)x.dxh + (double)x.dxl;
+                                         std::max(L, 1), lq, scale);
+    out[0] = x.ncell > 0 ? std::ldexp(c, x.shift) : 0.0;
     out[1] = (double)x.ncell;
     out[2] = x.ncell > 0 ? (double)x.ncut : 0.0;
     return KSC_OK;
@@ -767,14 +825,9 @@ int ksc_conv_real_multimap_stage(const ksc_split *s, const float *d_in, float *d
         if (s->path == 1)
             e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, n_maps,
                                          stride, 0, nullptr, st);
-        else if (n_maps >= 16 && s->tensor != 1)
-            e = ksc::launch_conv_sym_mma(s->plan, s->d_items_sym_lpt, s->n_items_sym, d_in, d_out,
-                                         n_maps, stride, s->n_items_belt > 0 ? 1 : 0, s->d_err,
-                                         st);
         else
-            e = ksc::launch_conv_sym(s->plan, s->d_items_sym_lpt, s->n_items_sym, d_in, d_out,
-                                     n_maps, stride, s->n_items_belt > 0 ? 1 : 0, 0,
-                                     s->plan.nrings - 1, st);
+            e = launch_caps(s, d_in, d_out, n_maps, stride, 0, (s->plan.nrings - 1) / 2, 0,
+                            s->plan.nrings - 1, n_maps >= 16, st);
     } else {
         return fail(KSC_ERR_ARG, "stage must be 1 or 2");
     }
@@ -796,8 +849,8 @@ int ksc_conv_real_stage(const ksc_split *s, const float *d_in, float *d_out, int
             e = ksc::launch_conv_general(s->plan, s->d_items, s->n_items, d_in, d_out, 1, 0, 0,
                                          nullptr, st);
         else
-            e = ksc::launch_conv_sym(s->plan, s->d_items_sym_lpt, s->n_items_sym, d_in, d_out, 1, 0,
-                                     s->n_items_belt > 0 ? 1 : 0, 0, s->plan.nrings - 1, st);
+            e = launch_caps(s, d_in, d_out, 1, 0, 0, (s->plan.nrings - 1) / 2, 0,
+                            s->plan.nrings - 1, false, st);
     } else {
         return fail(KSC_ERR_ARG, "stage must be 1 or 2");
     }

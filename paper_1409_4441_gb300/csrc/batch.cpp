@@ -12,11 +12,13 @@
 // and replayed; the map pointers live in a device entry table that a run
 // refreshes only when they change.
 //
-// The tile variants are the full and half block size of each kernel (belt:
-// 2080 or 1040 outputs per item; symmetric gather: 128 or 64 reflection
-// classes per item) and, for the gather, paired lanes (two lanes per class,
-// 64 classes per 128-thread item).  Half blocks suit short rings (a 1024-pixel
-// belt ring fills only half of a 2080-output item).  The autotuner times every
+// The tile variants are the full and half block size of the belt kernel
+// (2080 or 1040 outputs per item) and three gather tiles: 256 reflection
+// classes per item with 4096-cell weight tables (two CTAs per SM), 128 classes
+// with 2048-cell tables (three CTAs per SM; ring pairs needing more cells take
+// per-pair weights), and 128 classes with 4096-cell tables (two CTAs per SM).
+// Smaller items suit short rings (a 1024-pixel belt ring fills only half of a
+// 2080-output item, a ring of 512 pixels has 64 reflection classes).  The autotuner times every
 // variant of both kernels on every nside group of the batch, with the caller's
 // maps, keeps the fastest of each, and caches the choice per (device, nside,
 // l_max, table size, theta_cut) for the rest of the process.
@@ -53,9 +55,11 @@ TuneKey tune_key(const ksc_split *s) {
     return TuneKey(s->device, s->nside, s->lmax, s->n_int, bits);
 }
 
-// Untuned default: half blocks only where a belt ring is shorter than a full item.
+// Untuned default: half blocks only where a belt ring is shorter than a full
+// item; the single-map gather tile of that nside.
 std::pair<int, int> default_variants(const ksc_split *s) {
-    return {4 * s->nside <= ksc::belt_variant_chunk(1) ? 1 : 0, 0};
+    return {4 * s->nside <= ksc::belt_variant_chunk(1) ? 1 : 0,
+            ksc::sym_chunk(s->nside) == ksc::sym_variant_chunk(0) ? 0 : 2};
 }
 
 struct Launch {

@@ -12,28 +12,32 @@
 //   out[r,   kb + qQ] += w m[r',   kb' + qQ']      kb = Q - k - t, kb' = Q' - k' - t'
 //   and the same on the mirror rings r_s, r'_s.
 //
-// One thread owns one reflection class {k, kb} of first-quarter positions of
-// a northern ring (a class of one when kb coincides with k up to a quarter
-// turn) and produces all its images (no mirror on the equator ring, which is
-// its own mirror image).  Per input ring the CTA stages, for the union of its
-// threads' windows, the sixteen image sequences m[image(k')] in shared memory
-// so that every image of input position k' sits at the same offset; each
-// thread then walks its window four positions at a time: four independent
-// kernel weights, then one 16-byte shared load per image feeding four FFMAs.
-// A weight depends on the pixel pair only through the exact integer
-// N = (2k + t) L' - (2k' + t') L, dphi / 2 = N pi / (2 L L').  Per input ring
-// the CTA first builds the ring pair's weight table in dphi in shared memory
-// (cubic cells, each from the double-float chord and the K_r table at its two
-// ends, ksc_sym.cuh); a weight is then one cell lookup and three FMAs.  Ring
-// pairs without a table (whole-ring windows, or more cells than a CTA holds)
-// evaluate the double-float chord and the K_r table per pair (ksc_device.cuh).
-// FP32 partial sums over 32 positions are Kahan-folded into the totals.
+// One thread owns C consecutive reflection classes {k, kb} of first-quarter
+// positions of a northern ring (a class of one when kb coincides with k up to a
+// quarter turn) and produces all their images (no mirror on the equator ring,
+// which is its own mirror image).  Per input ring the CTA stages, for the union
+// of its threads' windows, the sixteen image sequences m[image(k')] in shared
+// memory so that every image of input position k' sits at the same offset; each
+// thread then walks the union of its classes' windows four positions at a time:
+// 4 C kernel weights, then one 16-byte shared load per image feeding 4 C FFMAs.
+// The sixteen images of a position are loaded once for the C classes: shared-
+// memory bandwidth to the lanes (a 16-byte load by a warp costs four wavefronts
+// whatever its addresses) is what bounds this gather, and C classes per thread
+// divide the image traffic per pixel pair by C.
 //
-// Paired lanes (tile variant 2): two adjacent lanes own one class.  Each
-// evaluates two of every four kernel weights, the pair swaps them with one
-// shuffle, and each lane accumulates one hemisphere (eight images).  The work
-// per class is the same; the accumulators per thread halve, so more warps fit
-// on an SM to hide the latency of the double-float chains.
+// A weight depends on the pixel pair only through the exact integer
+// N = (2k + t) L' - (2k' + t') L (dphi / 2 = N pi / (2 L L')).  Per input ring
+// the CTA first builds the ring pair's weight table in |N| in shared memory
+// (cubic cells of 2^shift integers whose last cell ends exactly at the cut,
+// followed by a zero cell, ksc_sym.cuh); a weight is then a table position
+// p = min(|N| + off, nct 2^shift) 2^-shift (exact), its cell floor(p) and offset
+// p - floor(p) (exact), one 16-byte cell load and three FMAs, and it is exactly
+// zero beyond the cut with no test.  Ring pairs without a table (whole-ring
+// windows, or more cells than a CTA holds) evaluate the double-float chord and
+// the K_r table per pair (ksc_device.cuh).  FP32 partial sums over 64 positions
+// are Kahan-folded into the totals.
+#include <cstdint>
+
 #include "ksc_device.cuh"
 #include "ksc_internal.h"
 #include "ksc_sym.cuh"
@@ -43,22 +47,20 @@ namespace {
 
 constexpr int kRingChunk = 32;  // ring-pair constants staged per pass
 constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, reflected}
-// Tile shape: T threads, LANES lanes per reflection class (1, or 2 for paired
-// lanes), SPAN staged input positions per segment (each image row padded by 4
-// floats), MINB resident CTAs per SM the register budget is set for.
-// XCAP: x-table cells held in dynamic shared memory (0: weights evaluated
-// directly for every pair).
-template <int T_, int LANES_, int SPAN_, int MINB_, int XCAP_> struct SymShape {
-    static constexpr int T = T_, LANES = LANES_, kSpan = SPAN_, MINB = MINB_;
+constexpr int kFold = 16;       // quads per FP32 partial sum (64 positions)
+// Tile shape: T threads of C classes each, SPAN staged input positions per
+// segment (each image row padded by 4 floats), MINB resident CTAs per SM the
+// register budget is set for, XCAP table cells in dynamic shared memory.
+template <int T_, int C_, int SPAN_, int MINB_, int XCAP_> struct SymShape {
+    static constexpr int T = T_, C = C_, kSpan = SPAN_, MINB = MINB_, kXCap = XCAP_;
     static constexpr int kStride = SPAN_ + 4;
-    static constexpr int kClasses = T_ / LANES_;      // classes per item
-    static constexpr int kImgT = kImg / LANES_;       // images per thread
-    static constexpr int kXCap = XCAP_;
+    static constexpr int kClasses = T_ * C_;
     static constexpr size_t kDynSmem = sizeof(float4) * (size_t)XCAP_;
 };
-using ShapeFull = SymShape<128, 1, 384, 4, kXCap>;  // variant 0
-using ShapeHalf = SymShape<64, 1, 256, 6, 0>;       // variant 1
-using ShapePair = SymShape<128, 2, 384, 5, 0>;      // variant 2
+using ShapeC3 = SymShape<128, 3, 640, 2, kXCap>;    // variant 0: 384 classes per item
+using ShapeSmall = SymShape<128, 1, 448, 3, 2048>;  // variant 1: 128 classes, 3 CTAs per SM
+using ShapeWide = SymShape<128, 1, 448, 2, kXCap>;  // variant 2: 128 classes, full tables
+static_assert(ShapeC3::kSpan % 4 == 0 && ShapeSmall::kSpan % 4 == 0, "quad-aligned spans");
 
 __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
     const float y = v - *comp;
@@ -67,95 +69,143 @@ __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
     *sum = tt;
 }
 
-// Row of thread image i in the staged block: images are ordered
-// [direct q0..q3 | mirror direct q0..q3 | reflected q0..q3 | mirror reflected];
-// with paired lanes, lane h (0 north, 1 south) takes rows 4h..4h+3 and 8+4h..
-__device__ __forceinline__ int img_row(int i, int lanes, int h) {
-    if (lanes == 1) return i;
-    return i < 4 ? 4 * h + i : 8 + 4 * h + (i - 4);
+// floor(a / b), ceil(a / b) for b > 0
+__device__ __forceinline__ int floor_div(int a, int b) {
+    const int q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+__device__ __forceinline__ int ceil_div(int a, int b) {
+    const int q = a / b;
+    return (a % b != 0 && a > 0) ? q + 1 : q;
 }
 
-// The four kernel weights of quad kq (positions kq .. kq + 3; zero outside
-// [a, b] and beyond the cut).  With paired lanes each lane evaluates two and
-// the pair swaps them.  Straight-line code: the evaluations interleave.
-// MODE 0: double-float chord with the general sine; 1: with the small-angle
-// sine; 2: the ring pair's x table (partial windows only: every position
-// outside [a, b] then lies beyond the cut, so the cut test alone zeroes it).
-template <class S, int MODE>
-__device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing &g,
-                                               const float4 *xt, int kq, int a, int b,
-                                               long long num, int L, int h, unsigned pair_mask) {
+// Sixteen (or, on the equator, eight) images of one quad of positions for the C
+// classes of a thread: one 16-byte shared load per image, 4 C FFMAs.
+template <class S, bool MIRROR>
+__device__ __forceinline__ void fma_quad(const float *st, int j, const float4 *w, float *part) {
+#pragma unroll
+    for (int i = 0; i < kImg; ++i) {
+        if (!MIRROR && (i & 4)) continue;
+        const float4 v = *reinterpret_cast<const float4 *>(st + i * S::kStride + j);
+#pragma unroll
+        for (int c = 0; c < S::C; ++c) {
+            float p = part[c * kImg + i];
+            p = fmaf(w[c].x, v.x, p);
+            p = fmaf(w[c].y, v.y, p);
+            p = fmaf(w[c].z, v.z, p);
+            p = fmaf(w[c].w, v.w, p);
+            part[c * kImg + i] = p;
+        }
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void fold(float *sum, float *comp, float *part) {
+#pragma unroll
+    for (int i = 0; i < S::C * kImg; ++i) {
+        kahan(&sum[i], &comp[i], part[i]);
+        part[i] = 0.0f;
+    }
+}
+
+// Constants of the table path for one ring pair: table positions are
+// p = min(|N| + off, nct 2^shift) 2^-shift.
+struct TabPos {
+    float inv, offS, ncf;  // 2^-shift, off 2^-shift, nct
+    float step, dcls;      // per position (2 L) and per class (2 L') in table units
+};
+
+// The four weights of the quad at table position tp (class c, first position).
+__device__ __forceinline__ float4 tab_quad(const float4 *xt, const TabPos &x, float tp) {
+    float4 w;
+    w.x = xtab_at(xt, fminf(fabsf(tp) + x.offS, x.ncf));
+    w.y = xtab_at(xt, fminf(fabsf(tp - x.step) + x.offS, x.ncf));
+    w.z = xtab_at(xt, fminf(fabsf(fmaf(-2.0f, x.step, tp)) + x.offS, x.ncf));
+    w.w = xtab_at(xt, fminf(fabsf(fmaf(-3.0f, x.step, tp)) + x.offS, x.ncf));
+    return w;
+}
+
+// Table path.  Positions a..b of one staged segment (s0: its first position):
+// the union of the thread's classes' windows within the cut.  Every weight
+// beyond a class's cut is exactly zero (the table's zero cell), so no position
+// needs a mask.  The loop is software-pipelined: the next quad's weights are
+// looked up while the current quad's FFMAs run.
+template <class S, bool MIRROR>
+__device__ __forceinline__ void acc_table(const float4 *xt, const TabPos &x, const float *st,
+                                          int s0, int a, int b, int num, int L, float *sum,
+                                          float *comp, float *part) {
+    constexpr int C = S::C;
+    int kq = s0 + ((a - s0) & ~3);
+    // exact: the thread's positions lie within a few of every class's window, where
+    // |N| < 2^24
+    float tp = (float)(num - 2 * L * kq) * x.inv;  // class 0 at the first quad
+    float4 wc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) wc[c] = tab_quad(xt, x, fmaf((float)c, x.dcls, tp));
+    int nq = 0;
+    for (; kq + 4 <= b; kq += 4) {
+        tp = fmaf(-4.0f, x.step, tp);
+        float4 wn[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) wn[c] = tab_quad(xt, x, fmaf((float)c, x.dcls, tp));
+        fma_quad<S, MIRROR>(st, kq - s0, wc, part);
+#pragma unroll
+        for (int c = 0; c < C; ++c) wc[c] = wn[c];
+        if (++nq == kFold) {
+            nq = 0;
+            fold<S>(sum, comp, part);
+        }
+    }
+    fma_quad<S, MIRROR>(st, kq - s0, wc, part);  // the last quad (kq <= b < kq + 4)
+    fold<S>(sum, comp, part);
+}
+
+// Per-pair path (no table): the four kernel weights of quad kq (zero outside
+// [a, b] and beyond the cut); MODE 0: double-float chord with the general sine,
+// 1: with the small-angle sine.  Straight-line code: the evaluations interleave.
+template <int MODE>
+__device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing &g, int kq,
+                                               int a, int b, long long num, int L) {
     const float N0 = (float)(num - 2LL * kq * L);  // exact integer below 2^24
     const float step = (float)(2 * L);
-    float w[4];
-    constexpr int NE = 4 / S::LANES;  // weights evaluated by this lane
-#pragma unroll
-    for (int ee = 0; ee < NE; ++ee) {
-        const int e = S::LANES == 2 ? 2 * h + ee : ee;
-        const float Nf = N0 - (float)e * step;
-        if constexpr (MODE == 2)
-            w[ee] = xtab_weight(xt, g, Nf);
-        else
-            w[ee] = sym_weight<MODE == 1>(P, g, Nf, kq + e, a, b);
-    }
-    if constexpr (S::LANES == 2) {  // swap halves with the partner lane
-        const float o0 = __shfl_xor_sync(pair_mask, w[0], 1);
-        const float o1 = __shfl_xor_sync(pair_mask, w[1], 1);
-        if (h == 0) { w[2] = o0; w[3] = o1; }
-        else { w[2] = w[0]; w[3] = w[1]; w[0] = o0; w[1] = o1; }
-    }
-    return make_float4(w[0], w[1], w[2], w[3]);
+    return make_float4(sym_weight<MODE == 1>(P, g, N0, kq, a, b),
+                       sym_weight<MODE == 1>(P, g, N0 - step, kq + 1, a, b),
+                       sym_weight<MODE == 1>(P, g, N0 - 2.0f * step, kq + 2, a, b),
+                       sym_weight<MODE == 1>(P, g, N0 - 3.0f * step, kq + 3, a, b));
 }
 
-// Positions a..b of one staged segment (starting at s0) for one thread.  The
-// loop is software-pipelined: the weights of the next quad (table lookups, or
-// double-float chains) are evaluated while the current quad's weights feed the
-// FFMAs.
+// Positions a..b of one segment for classes c = 0..C-1 with windows
+// [lo[c], hi[c]] (num of class c = num0 + 2 c L2).
 template <class S, bool MIRROR, int MODE>
-__device__ __forceinline__ void accumulate(const ConvPlan &P, const SymRing &g, const float4 *xt,
-                                           const float *st, int s0, int a, int b, long long num,
-                                           int L, float *sum, float *comp) {
-    constexpr int kStride = S::kStride, NI = S::kImgT;
-    const int h = S::LANES == 2 ? (threadIdx.x & 1) : 0;
-    const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1);
-    const bool idle = S::LANES == 2 && !MIRROR && h == 1;  // no south images on the equator
-    float part[NI];
-#pragma unroll
-    for (int i = 0; i < NI; ++i) part[i] = 0.0f;
+__device__ __forceinline__ void acc_pairs(const ConvPlan &P, const SymRing &g, const float *st,
+                                          int s0, int a, int b, long long num0, int L,
+                                          const int *lo, const int *hi, float *sum, float *comp,
+                                          float *part) {
+    constexpr int C = S::C;
     int nq = 0;
-    int kq = s0 + ((a - s0) & ~3);
-    if (kq > b) return;
-    float4 wc = quad_weights<S, MODE>(P, g, xt, kq, a, b, num, L, h, pair_mask);
-    for (; kq <= b; kq += 4) {
-        // next quad's weights (past b they are zero and unused)
-        const float4 wn = quad_weights<S, MODE>(P, g, xt, kq + 4, a, b, num, L, h, pair_mask);
-        const int j = kq - s0;
-        if (!idle) {
+    for (int kq = s0 + ((a - s0) & ~3); kq <= b; kq += 4) {
+        // (rare: one class at a time, each loading the images again)
 #pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                const int img = img_row(i, S::LANES, h);
-                if (S::LANES == 1 && !MIRROR && (img & 4)) continue;
-                const float4 v = *reinterpret_cast<const float4 *>(st + img * kStride + j);
-                float p = part[i];
-                p = fmaf(wc.x, v.x, p);
-                p = fmaf(wc.y, v.y, p);
-                p = fmaf(wc.z, v.z, p);
-                p = fmaf(wc.w, v.w, p);
-                part[i] = p;
+        for (int c = 0; c < C; ++c) {
+            const float4 w = quad_weights<MODE>(P, g, kq, lo[c], hi[c], num0 + 2LL * c * g.len, L);
+#pragma unroll
+            for (int i = 0; i < kImg; ++i) {
+                if (!MIRROR && (i & 4)) continue;
+                const float4 v = *reinterpret_cast<const float4 *>(st + i * S::kStride + kq - s0);
+                float pp = part[c * kImg + i];
+                pp = fmaf(w.x, v.x, pp);
+                pp = fmaf(w.y, v.y, pp);
+                pp = fmaf(w.z, v.z, pp);
+                pp = fmaf(w.w, v.w, pp);
+                part[c * kImg + i] = pp;
             }
         }
-        wc = wn;
-        if (++nq == 8) {  // fold every 32 positions
+        if (++nq == kFold) {
             nq = 0;
-#pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                kahan(&sum[i], &comp[i], part[i]);
-                part[i] = 0.0f;
-            }
+            fold<S>(sum, comp, part);
         }
     }
-#pragma unroll
-    for (int i = 0; i < NI; ++i) kahan(&sum[i], &comp[i], part[i]);
+    fold<S>(sum, comp, part);
 }
 
 template <class S, bool MIRROR>
@@ -164,21 +214,17 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                                          int band_hi, const float *__restrict__ m,
                                          float *__restrict__ o, SymRing *sR, float *st,
                                          float4 *xt) {
-    constexpr int T = S::T, kSpan = S::kSpan, kStride = S::kStride, NI = S::kImgT;
+    constexpr int T = S::T, C = S::C, kSpan = S::kSpan, kStride = S::kStride;
     const int tid = threadIdx.x;
-    const int h = S::LANES == 2 ? (tid & 1) : 0;  // paired lanes: hemisphere
     const DevRing R = P.d_rings[r];
     const int L = R.len, Q = L / 4, t = R.phase;
     const int2 rg = P.d_range[r];
-    const int k = c0 + tid / S::LANES;
-    const bool active = k < n_cls;
+    const int k0 = c0 + C * tid;  // this thread's first class
+    const bool active = k0 < n_cls;
     const int k_first = c0, k_last = min(c0 + S::kClasses, n_cls) - 1;
-    // reflection partner of k; none when it is k itself up to a quarter turn
-    const int kb = Q - k - t;
-    const bool refl = kb != k && kb != Q;
-    float sum[NI], comp[NI];
+    float sum[C * kImg], comp[C * kImg], part[C * kImg];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) sum[i] = comp[i] = 0.0f;
+    for (int i = 0; i < C * kImg; ++i) sum[i] = comp[i] = part[i] = 0.0f;
 
     for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
         const int nq = min(kRingChunk, rg.y - q0 + 1);
@@ -189,16 +235,30 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             const SymRing g = sR[qi];
             if (g.hw < 0.0f) continue;
             const int L2 = g.len, Q2 = L2 / 4;
-            long long num, numx;
-            int klo, khi, U0, U1, dummy;
-            sym_window(k, t, L, g, &num, &klo, &khi);
+            long long num0, numx;
+            int lo[C], hi[C], U0, U1, dummy;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                long long nc;
+                sym_window(k0 + c, t, L, g, &nc, &lo[c], &hi[c]);
+                if (c == 0) num0 = nc;
+            }
             sym_window(k_first, t, L, g, &numx, &U0, &dummy);
             sym_window(k_last, t, L, g, &numx, &dummy, &U1);
-            const bool use_xt = S::kXCap > 0 && g.ncell > 0 && g.ncell <= S::kXCap;
-            if (use_xt) {  // (the segment's first barrier publishes the table)
+            // table with its last cell ending at the cut (plus one zero cell)
+            const int off = (-(g.ncut + 1)) & ((1 << g.shift) - 1);
+            const int nct = (g.ncut + 1 + off) >> g.shift;
+            const bool use_xt = g.ncell > 0 && nct + 1 <= S::kXCap;
+            // the union of this thread's classes' windows (within the cut for tables)
+            int wa = lo[0], wb = hi[C - 1];
+            if (use_xt) {
+                wa = max(wa, ceil_div((int)num0 - g.ncut, 2 * L));
+                wb = min(wb, floor_div((int)(num0 + 2LL * (C - 1) * L2) + g.ncut, 2 * L));
                 __syncthreads();  // the previous ring pair's lookups are done
-                xtab_build<S::T>(P, g, xt);
+                xtab_build_cut<S::T>(P, g, xt, off, nct);  // (published by the next barrier)
             }
+            const TabPos x{g.inv, (float)off * g.inv, (float)nct, (float)(2 * L) * g.inv,
+                           (float)(2 * L2) * g.inv};
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 // positions this segment needs (the union ends at U1)
                 const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
@@ -223,24 +283,30 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 }
                 __syncthreads();
                 if (!active) continue;
-                const int a = max(klo, s0), b = min(khi, s0 + kSpan - 1);
+                const int a = max(wa, s0), b = min(wb, s0 + span - 1);
                 if (a > b) continue;
                 // (classes without a reflection partner accumulate the reflected
                 // images too; those sums are never written)
-                if (S::kXCap > 0 && use_xt)
-                    accumulate<S, MIRROR, 2>(P, g, xt, st, s0, a, b, num, L, sum, comp);
+                if (use_xt)
+                    acc_table<S, MIRROR>(xt, x, st, s0, a, b, (int)num0, L, sum, comp, part);
                 else if (g.small)
-                    accumulate<S, MIRROR, 1>(P, g, xt, st, s0, a, b, num, L, sum, comp);
+                    acc_pairs<S, MIRROR, 1>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
                 else
-                    accumulate<S, MIRROR, 0>(P, g, xt, st, s0, a, b, num, L, sum, comp);
+                    acc_pairs<S, MIRROR, 0>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
             }
         }
     }
-    if (active) {
-        const int rs = P.nrings - 1 - r;
-        const int start_s = P.d_rings[rs].start;
-        const bool wn = r >= band_lo && r <= band_hi;
-        const bool ws = MIRROR && rs >= band_lo && rs <= band_hi;
+    const int rs = P.nrings - 1 - r;
+    const int start_s = P.d_rings[rs].start;
+    const bool wn = r >= band_lo && r <= band_hi;
+    const bool ws = MIRROR && rs >= band_lo && rs <= band_hi;
+#pragma unroll
+    for (int cl = 0; cl < C; ++cl) {
+        const int k = k0 + cl;
+        if (k >= n_cls) break;
+        // reflection partner of k; none when it is k itself up to a quarter turn
+        const int kb = Q - k - t;
+        const bool refl = kb != k && kb != Q;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (c == 1 && !refl) break;
@@ -248,26 +314,16 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int kq = kk + qq * Q;
-                if (S::LANES == 1) {
-                    const float vn = sum[8 * c + qq] * P.domega;
-                    if (wn) {
-                        if (add) o[R.start + kq] += vn;
-                        else o[R.start + kq] = vn;
-                    }
-                    if constexpr (MIRROR) {
-                        const float vs = sum[8 * c + 4 + qq] * P.domega;
-                        if (ws) {
-                            if (add) o[start_s + kq] += vs;
-                            else o[start_s + kq] = vs;
-                        }
-                    }
-                } else {  // lane h writes its hemisphere
-                    const float v = sum[4 * c + qq] * P.domega;
-                    const bool wr = h == 0 ? wn : ws;
-                    const int base = h == 0 ? R.start : start_s;
-                    if (wr) {
-                        if (add) o[base + kq] += v;
-                        else o[base + kq] = v;
+                const float vn = sum[cl * kImg + 8 * c + qq] * P.domega;
+                if (wn) {
+                    if (add) o[R.start + kq] += vn;
+                    else o[R.start + kq] = vn;
+                }
+                if constexpr (MIRROR) {
+                    const float vs = sum[cl * kImg + 8 * c + 4 + qq] * P.domega;
+                    if (ws) {
+                        if (add) o[start_s + kq] += vs;
+                        else o[start_s + kq] = vs;
                     }
                 }
             }
@@ -352,7 +408,7 @@ int sm_count_sym() {
     return n_sm;
 }
 
-// Grid of a persistent launch; the kernel's dynamic shared memory (the x table)
+// Grid of a persistent launch; the kernel's dynamic shared memory (the table)
 // is enabled on first use.
 template <class K>
 cudaError_t sym_grid(K kernel, int threads, size_t dyn_smem, int n_items, int per_sm_cap,
@@ -371,18 +427,10 @@ cudaError_t sym_grid(K kernel, int threads, size_t dyn_smem, int n_items, int pe
     return cudaSuccess;
 }
 
-} // namespace
-
-int sym_classes(int len, int phase) {
-    const int Q = len / 4;
-    return phase ? (Q + 1) / 2 : Q / 2 + 1;
-}
-
-cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
-                            const float *d_in, float *d_out, int n_maps, long long map_stride,
-                            int belt_split, int band_lo, int band_hi, cudaStream_t st) {
-    if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
-    using S = ShapeFull;
+template <class S>
+cudaError_t sym_launch(const ConvPlan &p, const WorkItem *d_items, int n_items,
+                       const float *d_in, float *d_out, int n_maps, long long map_stride,
+                       int belt_split, int band_lo, int band_hi, cudaStream_t st) {
     int blocks = 0;
     cudaError_t e = sym_grid(conv_sym_kernel<S>, S::T, S::kDynSmem, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
@@ -402,13 +450,33 @@ cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_it
     return e != cudaSuccess ? e : f;
 }
 
-int sym_chunk() { return ShapeFull::kClasses; }
+} // namespace
+
+int sym_classes(int len, int phase) {
+    const int Q = len / 4;
+    return phase ? (Q + 1) / 2 : Q / 2 + 1;
+}
+
+// Single-map items: 384 classes (3 per thread) where rings are long enough for
+// many of them (nside >= 2048), else 128 (smaller items balance a launch better).
+int sym_chunk(int nside) { return nside >= 2048 ? ShapeC3::kClasses : ShapeWide::kClasses; }
+
+cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
+                            const float *d_in, float *d_out, int n_maps, long long map_stride,
+                            int belt_split, int band_lo, int band_hi, cudaStream_t st) {
+    if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
+    if (sym_chunk(p.nside) == ShapeC3::kClasses)
+        return sym_launch<ShapeC3>(p, d_items, n_items, d_in, d_out, n_maps, map_stride,
+                                   belt_split, band_lo, band_hi, st);
+    return sym_launch<ShapeWide>(p, d_items, n_items, d_in, d_out, n_maps, map_stride,
+                                 belt_split, band_lo, band_hi, st);
+}
 
 int sym_variants() { return 3; }
 
 int sym_variant_chunk(int variant) {
-    return variant == 2 ? ShapePair::kClasses
-                        : (variant == 1 ? ShapeHalf::kClasses : ShapeFull::kClasses);
+    return variant == 0 ? ShapeC3::kClasses
+                        : (variant == 1 ? ShapeSmall::kClasses : ShapeWide::kClasses);
 }
 
 template <class S>
@@ -429,13 +497,13 @@ cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
                                   int per_sm_cap, int *d_counter, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
     if (variant == 2)
-        return sym_batch_launch<ShapePair>(d_plans, d_entries, d_items, n_items, per_sm_cap,
+        return sym_batch_launch<ShapeWide>(d_plans, d_entries, d_items, n_items, per_sm_cap,
                                            d_counter, st);
     if (variant == 1)
-        return sym_batch_launch<ShapeHalf>(d_plans, d_entries, d_items, n_items, per_sm_cap,
-                                           d_counter, st);
-    return sym_batch_launch<ShapeFull>(d_plans, d_entries, d_items, n_items, per_sm_cap,
-                                       d_counter, st);
+        return sym_batch_launch<ShapeSmall>(d_plans, d_entries, d_items, n_items, per_sm_cap,
+                                            d_counter, st);
+    return sym_batch_launch<ShapeC3>(d_plans, d_entries, d_items, n_items, per_sm_cap,
+                                     d_counter, st);
 }
 
 } // namespace ksc

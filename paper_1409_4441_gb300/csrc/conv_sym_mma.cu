@@ -126,6 +126,7 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
     __shared__ __align__(8) uint64_t mdone[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
+    __shared__ int s_drained;  // 0: an MMA outlived the bounded drain
 
     const int tid = threadIdx.x, warp = tid >> 5;
     // Epilogue (tensor memory) mapping: a warp reaches TMEM lanes 32 (warp % 4) ..
@@ -147,6 +148,7 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
         tc::mbar_init(&mdone[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
+        s_drained = 1;
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -236,10 +238,15 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 load_b(src_base, qoff, live, reflected, P0, pg, L2, Q2, g.phase, bv);
                 for (int u = 0; u < n_tiles; ++u) {
                     const int b = tcount & 1;
+                    bool stage_free = true;
                     if (pending[b]) {  // the MMAs that last read this stage are done
-                        if (!tc::mbar_wait(&mdone[b], ph_done[b])) s_abort = 1;
-                        ph_done[b] ^= 1u;
-                        pending[b] = 0;
+                        if (tc::mbar_wait(&mdone[b], ph_done[b])) {
+                            ph_done[b] ^= 1u;
+                            pending[b] = 0;
+                        } else {  // still pending: write nothing into the stage
+                            s_abort = 1;
+                            stage_free = false;
+                        }
                     }
                     Stage &S = stage[b];
                     const int pbase = P0 + u * kKT;
@@ -247,17 +254,22 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     if (u + 1 < n_tiles)
                         load_b(src_base, qoff, live, reflected, pbase + kKT, pg, L2, Q2, g.phase,
                                bn);
-                    if (use_xt)
+                    if (!stage_free) {
+                    } else if (use_xt) {
                         build_a<2>(P, g, xt, S, brow, bpart, pbase, num, L, klo, khi);
-                    else if (g.small)
+                    } else if (g.small) {
                         build_a<1>(P, g, xt, S, brow, bpart, pbase, num, L, klo, khi);
-                    else
+                    } else {
                         build_a<0>(P, g, xt, S, brow, bpart, pbase, num, L, klo, khi);
+                    }
+                    if (stage_free) {
 #pragma unroll
-                    for (int i = 0; i < 2; ++i)
-                        store_split4(S.b_hi, S.b_lo, tc::toff<kKT>(8 * warp + sub + 4 * i, 4 * pg),
-                                     make_float4(bv[4 * i], bv[4 * i + 1], bv[4 * i + 2],
-                                                 bv[4 * i + 3]));
+                        for (int i = 0; i < 2; ++i)
+                            store_split4(S.b_hi, S.b_lo,
+                                         tc::toff<kKT>(8 * warp + sub + 4 * i, 4 * pg),
+                                         make_float4(bv[4 * i], bv[4 * i + 1], bv[4 * i + 2],
+                                                     bv[4 * i + 3]));
+                    }
 #pragma unroll
                     for (int j = 0; j < 8; ++j) bv[j] = bn[j];
                     tc::fence_async_smem();
@@ -290,9 +302,12 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                 for (int bb = 0; bb < 2; ++bb) {
                     const int b = (tcount + bb) & 1;  // older stage first
                     if (pending[b]) {
-                        if (!tc::mbar_wait(&mdone[b], ph_done[b])) s_abort = 1;
-                        ph_done[b] ^= 1u;
-                        pending[b] = 0;
+                        if (tc::mbar_wait(&mdone[b], ph_done[b])) {
+                            ph_done[b] ^= 1u;
+                            pending[b] = 0;
+                        } else {
+                            s_abort = 1;
+                        }
                     }
                 }
                 __syncthreads();
@@ -355,12 +370,14 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
     }
     if (!ok) {
         if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
-        for (int b = 0; b < 2; ++b)  // bounded drain of MMAs still in flight
-            if (pending[b]) tc::mbar_wait(&mdone[b], ph_done[b]);
+        // bounded drain of MMAs still in flight; if one never completes, the tensor
+        // memory it may still write is not freed (see s_drained)
+        for (int b = 0; b < 2; ++b)
+            if (pending[b] && !tc::mbar_wait(&mdone[b], ph_done[b])) s_drained = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0 && s_drained)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
 }
@@ -368,6 +385,8 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
 } // namespace
 
 int sym_mma_maps() { return kMaps; }
+
+int sym_mma_chunk() { return kM; }
 
 cudaError_t launch_conv_sym_mma(const ConvPlan &p, const WorkItem *d_items, int n_items,
                                 const float *d_in, float *d_out, int n_maps,

@@ -39,28 +39,41 @@ struct PairInfo {
 };
 
 // Weight table of one ring pair for the symmetric gather.  For a fixed ring
-// pair the kernel weight depends on the pixel pair only through
-// x = dphi / 2 = |N| c, so it is tabulated in x: ncell cubic cells of width dx
-// (kXRho table intervals of the chord each at most, stretched up to kXRhoMax
-// where that many cells would not fit a CTA's kXCap), cell position
-// p = |N| c / dx = |N| R.  Pairs with |N| <= ncut lie within the cut.
-// ncell = 0: no table (whole-ring windows, or more cells than a CTA holds).
+// pair the kernel weight depends on the pixel pair only through the exact
+// integer |N| (x = dphi / 2 = |N| c), so it is tabulated in |N|: cubic cells of
+// 2^shift consecutive integers each, cell j covering j 2^shift <= |N| <
+// (j + 1) 2^shift.  Because the width is a power of two, the cell of a pair and
+// its offset in the cell, (|N| mod 2^shift) / 2^shift, are exact in FP32
+// arithmetic (|N| < 2^24).  The width is the largest power of two that keeps a
+// cell within kXRho intervals of the K_r table (in the chord) where the chord
+// changes fastest, doubled (up to kXRhoMax intervals) while the cells would not
+// fit a CTA's kXCap.  Pairs with |N| <= ncut lie within the cut.  ncell cells
+// hold the cubic coefficients; the gather may read (without using) up to
+// kXPad(L) cells beyond them, L the output ring's length.  ncell = 0: no table
+// (whole-ring windows, or more cells than a CTA holds).
 struct XInfo {
-    float dxh, dxl;  // dx as a double-float pair
-    float Rh, Rl;    // R = c / dx as a double-float pair
-    float ncut;      // largest |N| within the cut (an exact integer)
-    float pmax;      // ncell - 0.5: cell positions are clamped below it
-    int ncell, pad;
+    int shift;  // cell width 2^shift in |N|
+    int ncut;   // largest |N| within the cut
+    int ncell;  // cells written (0: no table)
+    int pad;
 };
-constexpr double kXRho = 2.0;     // chord-table intervals per x cell (at most) ...
+constexpr double kXRho = 2.0;     // chord-table intervals per cell (at most) ...
 constexpr double kXRhoMax = 3.0;  // ... unless the cells would not fit
-constexpr int kXCap = 1792;    // cells a CTA holds in shared memory (28 kB)
+constexpr int kXCap = 4096;       // cells the largest gather tile holds (64 kB)
+// Cells beyond ncell an edge quad of four positions may read: a quad reaches
+// at most 3 positions (|N| steps of 2 L) past the cut.
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int kXPad(int L, int shift) { return ((6 * L) >> shift) + 2; }
 
-// Host: the x-table parameters of ring pair (r, q); A2, B2 are the ring-pair
-// constants scaled to table-position units, lq the input ring's length, hw the
-// window half-width (whole-ring windows get no table); scale <= 1 narrows the
-// cells of a table coarser than the automatic size (n_int / n_auto).
-XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int lq, double scale);
+// Host: the table parameters of ring pair (r, q); A2, B2 are the ring-pair
+// constants scaled to table-position units, c = pi / (2 L lq), L and lq the
+// output and input rings' lengths, hw the window half-width (whole-ring windows
+// get no table); scale <= 1 narrows the cells of a table coarser than the
+// automatic size (n_int / n_auto).
+XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int L, int lq,
+                 double scale);
 
 // ---------------------------------------------------------------------------
 // Host FP64 split fit (Sec. 2, Eq. 1-6).
@@ -153,8 +166,8 @@ cudaError_t launch_conv_belt_mma(const ConvPlan &p, const int2 *d_items, int n_i
 // Symmetric gather over northern rings (and the equator): each thread owns
 // one first-quarter position and writes its eight images; only output rings
 // in [band_lo, band_hi] are written.  Items are (ring, first quarter position)
-// chunks of sym_chunk().
-int sym_chunk();
+// chunks of sym_chunk(nside) classes (the tile launch_conv_sym uses for that nside).
+int sym_chunk(int nside);
 int sym_classes(int len, int phase);  // reflection classes of a ring's first quarter
 // CTAs claim items in list order through per-call counters taken from the
 // stream-ordered allocator.
@@ -190,9 +203,19 @@ cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
                                   int per_sm_cap, int *d_counter, cudaStream_t st);
 
 // tcgen05 gather for map stacks (symmetric ring pairs): items are the
-// symmetric work items (sym_chunk() classes each); maps in groups of
+// symmetric work items of sym_mma_chunk() classes each; maps in groups of
 // sym_mma_maps(); same outputs as launch_conv_sym over the whole map.
 int sym_mma_maps();
+int sym_mma_chunk();
+
+// tcgen05 gather for single maps (grid.y over maps of a stack): items of
+// sym_tc_chunk() classes (the same items as the map-stack kernel); same outputs
+// as launch_conv_sym, written for output rings in [band_lo, band_hi].
+int sym_tc_chunk();
+cudaError_t launch_conv_sym_tc(const ConvPlan &p, const WorkItem *d_items, int n_items,
+                               const float *d_in, float *d_out, int n_maps, long long map_stride,
+                               int belt_split, int band_lo, int band_hi, int *d_err,
+                               cudaStream_t st);
 cudaError_t launch_conv_sym_mma(const ConvPlan &p, const WorkItem *d_items, int n_items,
                                 const float *d_in, float *d_out, int n_maps,
                                 long long map_stride, int belt_split, int *d_err,
@@ -230,6 +253,11 @@ struct ksc_split {
     ksc::WorkItem *d_items_sym = nullptr;  // northern rings for the symmetric gather
     ksc::WorkItem *d_items_sym_lpt = nullptr;  // the same items, longest first (whole map)
     int n_items_sym = 0;
+    ksc::WorkItem *d_items_smma = nullptr;  // 128-class items of the tensor cap kernels,
+    ksc::WorkItem *d_items_smma_lpt = nullptr;  // in ring order and longest first
+    int n_items_smma = 0;
+    std::vector<int> ring_first_smma;
+    int cap_kernel = 0;                    // ksc_split_opts.cap_kernel
     std::vector<int> ring_first_sym;
     int path = 0;                          // 0: belt + symmetric, 1: general only
     int2 *d_items_belt = nullptr;          // belt chunks for the circulant kernel

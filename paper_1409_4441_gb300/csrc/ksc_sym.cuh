@@ -18,9 +18,10 @@ struct SymRing {  // one (output ring, input ring) pair
     DF A, B, c;
     float hw;     // half window in input pixels; < 0: no pixel within the cut
     int len, start, start_m, phase, small;
-    DF dx, R;     // x table (XInfo): cell width, cell position per unit |N|
-    float ncut, pmax;
-    int ncell;    // 0: no x table
+    // table in |N| (XInfo): cells of 2^shift integers, |N| <= ncut within the cut
+    int shift, ncut, ncell;  // ncell 0: no table
+    float inv;    // 2^-shift
+    float pcl;    // ncut 2^-shift: the largest in-cut table position
 };
 
 __device__ __forceinline__ int sym_pmod(int a, int n) {
@@ -47,11 +48,11 @@ __device__ __forceinline__ SymRing load_sym_ring(const ConvPlan &P, int r, int q
     g.small = (2.0f * pi.hw + 3.0f < (float)Qr.len) &&
               ((pi.hw + 1.0f) * 3.14159265f / (float)Qr.len < 0.25f);
     const XInfo xi = P.d_xinfo[P.d_pair_base[r] + (q - rg.x)];
-    g.dx = DF{xi.dxh, xi.dxl};
-    g.R = DF{xi.Rh, xi.Rl};
+    g.shift = xi.shift;
     g.ncut = xi.ncut;
-    g.pmax = xi.pmax;
     g.ncell = g.hw < 0.0f ? 0 : xi.ncell;
+    g.inv = __int_as_float((127 - xi.shift) << 23);  // 2^-shift
+    g.pcl = (float)xi.ncut * g.inv;
     return g;
 }
 
@@ -94,15 +95,15 @@ __device__ __forceinline__ float sym_weight(const ConvPlan &P, const SymRing &g,
     return (in && kp >= a && kp <= b) ? wv : 0.0f;
 }
 
-// x table of one ring pair (XInfo): the weight at cell boundary j, x = j dx,
-// and its slope per cell, from the same double-float chord and K_r table as
-// sym_weight.  Boundaries past the cut extrapolate the table's last cubic, so
-// the cell that holds the cut interpolates a smooth function.
+// Table of one ring pair (XInfo): the weight at cell boundary j, |N| = j 2^shift,
+// x = |N| c, and its slope per cell, from the same double-float chord and K_r
+// table as sym_weight.  Boundaries past the cut extrapolate the K_r table's last
+// cubic, so the cell that holds the cut interpolates a smooth function.
 __device__ __forceinline__ void xtab_node(const ConvPlan &P, const SymRing &g, int j, float *w,
-                                          float *d) {
-    const float jf = (float)j;
-    const float xh = jf * g.dx.h;
-    const float xl = fmaf(jf, g.dx.h, -xh) + jf * g.dx.l;
+                                          float *d, int off = 0) {
+    const float Nf = (float)((j << g.shift) - off);  // exact: below 2^24
+    const float xh = Nf * g.c.h;
+    const float xl = fmaf(Nf, g.c.h, -xh) + Nf * g.c.l;
     const DF s = sin_df(xh, xl);
     const float s2h = s.h * s.h;
     const float s2l = fmaf(2.0f * s.h, s.l, fmaf(s.h, s.h, -s2h));
@@ -117,15 +118,15 @@ __device__ __forceinline__ void xtab_node(const ConvPlan &P, const SymRing &g, i
     const float ul = (fmaf(-uh, uh, dh) + dl) * (0.5f * rr);
     const int i = max(0, min((int)floorf(uh), P.n_int - 1));
     const float f = (uh - (float)i) + ul;
-    const float4 c = __ldg(&P.d_tab[i]);
-    *w = hermite(c, f);
-    const float dk = fmaf(f, fmaf(f, 3.0f * c.w, 2.0f * c.z), c.y);  // dK/du
+    const float4 cf = __ldg(&P.d_tab[i]);
+    *w = hermite(cf, f);
+    const float dk = fmaf(f, fmaf(f, 3.0f * cf.w, 2.0f * cf.z), cf.y);  // dK/du
     // (the slope needs no more than the fast cosine: absolute error ~5e-7)
-    const float dudx = g.B.h * s.h * __cosf(xh) / fmaxf(uh, 1e-30f);
-    *d = dk * dudx * g.dx.h;
+    const float dudx = g.B.h * s.h * __cosf(xh) * rr;  // rr = 1 / u
+    *d = dk * dudx * (g.c.h * (float)(1 << g.shift));  // per cell: dx = 2^shift c
 }
 
-// The ring pair's x table in shared memory, built by the T threads of a CTA:
+// The ring pair's table in shared memory, built by the T threads of a CTA:
 // cell j holds the cubic coefficients (in the cell offset) from the weights and
 // slopes at boundaries j and j + 1.  Each thread fills a run of consecutive
 // cells (every boundary but the run's first evaluated once; an odd run length
@@ -148,19 +149,47 @@ __device__ __forceinline__ void xtab_build(const ConvPlan &P, const SymRing &g, 
     }
 }
 
-// Weight of the pixel pair with exact integer Nf from the x table xt (cubic
-// coefficients per cell); zero beyond the cut.
+// The same table with its cell boundaries moved down by `off` integers, so that
+// the last cell ends exactly at the cut: off = (-(ncut + 1)) mod 2^shift, cells
+// 0 .. nct - 1 cover |N| + off in [j 2^shift, (j + 1) 2^shift), nct = (ncut + 1 +
+// off) 2^-shift, and cell nct is zero.  A lookup at min(|N| + off, nct 2^shift)
+// is then K_r within the cut and exactly 0 beyond it, with no test.
+template <int T>
+__device__ __forceinline__ void xtab_build_cut(const ConvPlan &P, const SymRing &g, float4 *xt,
+                                               int off, int nct) {
+    const int per = ((nct + T - 1) / T) | 1;
+    const int j0 = threadIdx.x * per, j1 = min(j0 + per, nct);
+    if (threadIdx.x == 0) xt[nct] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (j0 >= j1) return;
+    float w0, d0;
+    xtab_node(P, g, j0, &w0, &d0, off);
+    for (int j = j0; j < j1; ++j) {
+        float w1, d1;
+        xtab_node(P, g, j + 1, &w1, &d1, off);
+        const float dw = w1 - w0;
+        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
+                            fmaf(-2.0f, dw, d0 + d1));
+        w0 = w1;
+        d0 = d1;
+    }
+}
+
+// Cubic of table position p = |N| 2^-shift (exact) from the table xt: cell
+// floor(p), offset p - floor(p).  p < 2^22, so adding 1.5 * 2^23 rounded
+// downward gives floor(p) in the low mantissa bits.
+__device__ __forceinline__ float xtab_at(const float4 *xt, float p) {
+    const float t = __fadd_rd(p, 12582912.0f);
+    const float4 cf = xt[__float_as_uint(t) - 0x4B400000u];
+    const float f = p - (t - 12582912.0f);
+    return hermite(cf, f);
+}
+
+// Weight of the pixel pair with exact integer Nf from the table xt; zero beyond
+// the cut (the position is clamped into the table first).
 __device__ __forceinline__ float xtab_weight(const float4 *xt, const SymRing &g, float Nf) {
     const float an = fabsf(Nf);
-    const float ph = an * g.R.h;
-    const float pl = fmaf(an, g.R.l, fmaf(an, g.R.h, -ph));
-    const float pc = fminf(ph, g.pmax);
-    const float t = (pc - 0.5f) + 12582912.0f;  // floor by the 1.5 * 2^23 rounding trick
-    const int j = __float_as_int(t) - 0x4B400000;
-    const float f = (pc - (t - 12582912.0f)) + pl;
-    const float4 c = xt[j];
-    const float v = hermite(c, f);
-    return an <= g.ncut ? v : 0.0f;
+    const float v = xtab_at(xt, fminf(an * g.inv, g.pcl));
+    return an <= (float)g.ncut ? v : 0.0f;
 }
 
 } // namespace ksc

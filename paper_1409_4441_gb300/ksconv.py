@@ -56,7 +56,7 @@ class Opts(ctypes.Structure):
                 ("svd_rcond", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("n_intervals", ctypes.c_int), ("path", ctypes.c_int),
                 ("tensor", ctypes.c_int), ("cut_continuity", ctypes.c_int),
-                ("exact_weights", ctypes.c_int)]
+                ("exact_weights", ctypes.c_int), ("cap_kernel", ctypes.c_int)]
 
 
 class Desc(ctypes.Structure):

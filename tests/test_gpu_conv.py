@@ -69,6 +69,7 @@ def test_table_matches_oracle_legendre_sum(K):
     assert np.abs(lib - exact).max() <= 3e-7 * peak
 
 
+@pytest.mark.parametrize("cap_kernel", [0, 1])
 @pytest.mark.parametrize("exact_weights", [0, 1])
 @pytest.mark.parametrize("nside,tc_deg,lmax,fwhm_deg", [
     (1, 60.0, 3, 40.0),      # twelve pixels, several per disc
@@ -77,13 +78,15 @@ def test_table_matches_oracle_legendre_sum(K):
     (32, 0.5, 95, 3.0),      # disc smaller than a pixel: only the self pair
     (64, 6.0, 191, 2.0),     # the 2-degree nside-64 workload (3 x FWHM cut)
 ])
-def test_full_map_parity(K, nside, tc_deg, lmax, fwhm_deg, exact_weights):
-    """Both weight paths of the cap gather: dphi tables (default) and the exact
-    double-float chord for every pair."""
+def test_full_map_parity(K, nside, tc_deg, lmax, fwhm_deg, exact_weights, cap_kernel):
+    """Both weight paths of the cap gather (tables in |N|, default, and the exact
+    double-float chord for every pair), each summed by both cap kernels (FP32 FFMAs,
+    default, and the tensor cores)."""
     tc = np.radians(tc_deg)
     c = inputs.gaussian_beam(lmax, np.radians(fwhm_deg))
     m = inputs.white_noise_map(nside, inputs.seed_for(1, nside)).astype(np.float32)
-    with K.make_split_real(c, nside, tc, exact_weights=exact_weights) as sp:
+    with K.make_split_real(c, nside, tc, exact_weights=exact_weights,
+                           cap_kernel=cap_kernel) as sp:
         n_int = K.split_info(sp)["n_intervals"]
         got = _run(K, sp, m)
     ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int))
@@ -114,6 +117,36 @@ def test_dphi_tables_match_exact_weights(K, nside, lmax, lcut, tc_deg, fwhm_deg)
     rms = np.sqrt(np.mean(yb ** 2))
     assert np.abs(ya - yb).max() <= 1e-6 * rms
     assert np.sqrt(np.mean((ya - yb) ** 2)) <= 1e-7 * rms
+
+
+@pytest.mark.parametrize("nside,lmax,lcut,tc_deg,fwhm_deg", [
+    (256, 767, 192, 2.0, 0.5),   # oscillating high-pass remainder, many cap ring pairs
+    (128, 383, 0, 12.0, 3.0),    # wide windows: several staged segments per ring pair
+])
+def test_tensor_caps_match_ffma_caps(K, nside, lmax, lcut, tc_deg, fwhm_deg):
+    """The cap ring pairs summed on the tensor cores (three-way BF16 splits, six MMAs
+    per 16 positions, a fresh accumulator per step) and by the FP32 FFMA gather with
+    the same weights: each within the per-pixel parity tolerance of the oracle on
+    sampled pixels, and the two within the sum of those tolerances of each other
+    everywhere (independent FP32 summation orders: a few ulp of the largest outputs)."""
+    tc = np.radians(tc_deg)
+    c = inputs.gaussian_beam(lmax, np.radians(fwhm_deg))
+    c[: lcut + 1] = 0.0
+    m = inputs.white_noise_map(nside, inputs.seed_for(1, 2000 + nside)).astype(np.float32)
+    with K.make_split_real(c, nside, tc, cap_kernel=1) as a, \
+            K.make_split_real(c, nside, tc) as b:
+        ya, yb = _run(K, a, m), _run(K, b, m)
+        K.device_status(a)
+        n_int = K.split_info(a)["n_intervals"]
+    pix = inputs.sample_pixels(nside, 1500, 29)
+    ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int),
+                            out_pix=pix)
+    _check(ya[pix], ref, amb)
+    _check(yb[pix], ref, amb)
+    rms = np.sqrt(np.mean(yb ** 2))
+    assert np.abs(ya - yb).max() <= 2e-6 * rms
+    # each path's FP32 summation error is about 1e-7 of the rms (rms over pixels)
+    assert np.sqrt(np.mean((ya - yb) ** 2)) <= 2e-7 * rms
 
 
 def test_self_pair_only(K):

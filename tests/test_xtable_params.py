@@ -1,18 +1,28 @@
-"""Host-side sizing of the symmetric gather's dphi weight tables (ksc_dphi_table_params,
+"""Host-side sizing of the symmetric gather's weight tables (ksc_dphi_table_params,
 no device work).
 
-For ring pairs of the HEALPix RING grid (geometry written out here from the public ring
-definitions) at the benchmark's cut and at a wide cut, the library's table must:
-cover every in-cut position (x = |N| c <= x_cut lies inside the cells); keep each cell at
-most 2 K_r-table intervals wide in the chord where 1792 cells allow it, and at most 3 where
-it stretches them (no table beyond); place the cut in |N| exactly; give whole-ring windows,
-pairs with no in-cut pixel and pairs entirely within the cut no table.  du/dx is sampled
-independently of the library's closed-form maximum.
+For a fixed ring pair the weight depends on the pixel pair only through the exact integer
+|N| (x = dphi / 2 = |N| c), and the library tabulates it in cubic cells of 2^shift
+integers.  For ring pairs of the HEALPix RING grid (geometry written out here from the
+public ring definitions) at the benchmark's cut and at a wide cut, the table must: cover
+every in-cut |N| (ncut >> shift < ncell) with room for the edge quads' reach of three
+positions (6 L in |N|) within the 4096 cells a CTA holds; use the widest power-of-two cell
+that stays within 2 K_r-table intervals of the chord and within the in-cut range (no node
+more than one cell past the cut, where the K_r table is extrapolated) where that fits, else
+the narrowest that fits, at most 3 intervals (no table beyond); place the cut in |N|
+exactly; give
+whole-ring windows, pairs with no in-cut pixel and pairs entirely within the cut no table.
+du/dx is sampled independently of the library's closed-form maximum.
 """
 import numpy as np
 import pytest
 
-CAP = 1792
+CAP = 4096
+
+
+def pad(L, shift):
+    """Cells an edge quad may read past the table: three positions, 6 L in |N|."""
+    return ((6 * L) >> shift) + 2
 
 
 @pytest.fixture(scope="module")
@@ -51,9 +61,10 @@ def pair(nside, i, iq, theta_cut, n_int):
     return A2, B2, np.pi / (2.0 * L * Lq), float(np.float32(hw)), Lq
 
 
-CASES = [  # nside, theta_cut, n_int, whether some pairs fit 2-interval cells:
+CASES = [  # nside, theta_cut, n_int, whether some pairs fit 2-interval cells
+          # (both do; the wide cut also stretches cells and leaves some pairs without one):
     (2048, np.radians(4.0), 4371, True),    # the benchmark's cut
-    (512, np.radians(16.0), 6590, False),   # a wide cut: cells stretched, or no table
+    (512, np.radians(16.0), 6590, True),    # a wide cut: some cells stretched
 ]
 
 
@@ -76,24 +87,36 @@ def test_table_cells_cover_the_cut_within_three_intervals(K, nside, theta_cut, n
         xs = np.linspace(0.0, xcut, 20001)
         u = np.sqrt(A2 + B2 * np.sin(xs) ** 2)
         dmax = np.max(B2 * np.sin(xs) * np.cos(xs) / np.maximum(u, 1e-300))
-        need = xcut * dmax / (CAP - 2)  # intervals per cell if the cells just fit
+        L = int(round(np.pi / (2 * c * lq)))
+        ncut = int(np.floor(xcut / c))
+        # the widest power-of-two cell within 2 intervals, and the narrowest that fits
+        s2 = 0
+        while (2 ** (s2 + 1)) * c * dmax <= 2.0 * (1 - 1e-6) and 2 ** (s2 + 1) <= ncut + 1:
+            s2 += 1
+        sf = s2
+        while (ncut >> sf) + 1 + pad(L, sf) > CAP:
+            sf += 1
         if t["ncell"] == 0:
-            assert need >= 3.0 * (1 - 1e-3), (i, iq, need)
+            assert sf > 0 and (2 ** sf) * c * dmax > 3.0 * (1 - 1e-3), (i, iq)
             seen["none"] += 1
             continue
         dx = t["dx"]
-        assert t["ncell"] <= CAP
-        # every in-cut position p = x / dx lies inside a cell, below the clamp at ncell - 0.5
-        assert xcut / dx <= (t["ncell"] - 1) * (1 + 1e-12)
-        assert dx * dmax <= 3.0 * (1 + 1e-6)  # at most 3 K_r-table intervals per cell
-        if need <= 2.0 * (1 - 1e-3):
-            assert dx * dmax <= 2.0 * (1 + 1e-6)  # 2 intervals where the cells fit
+        shift = int(round(np.log2(dx / c)))
+        assert dx == pytest.approx(c * 2.0 ** shift, rel=1e-14)  # a power-of-two cell
+        assert t["ncell"] == (t["ncut"] // 2 ** shift) + 1  # every in-cut |N| has a cell
+        assert t["ncell"] + pad(L, shift) <= CAP
+        assert shift == 0 or dx * dmax <= 3.0 * (1 + 1e-3)  # at most 3 intervals per cell
+        assert shift == 0 or 2 ** shift <= t["ncut"] + 1 or sf > s2  # no wider than the cut
+        if sf == s2:
+            assert shift == s2  # within 2 intervals where the cells fit
+            assert dx * dmax <= 2.0 * (1 + 1e-3) or shift == 0
             seen["table"] += 1
         else:
+            assert shift == sf
             seen["stretched"] += 1
         # the cut in |N|: the largest integer with |N| c <= x_cut
         N = t["ncut"]
-        assert N == np.floor(N)
+        assert N == ncut
         assert N * c <= xcut * (1 + 1e-12) and (N + 1) * c > xcut * (1 - 1e-12)
     assert seen["table"] + seen["stretched"] > 0
     assert (seen["table"] > 0) == fits
