@@ -50,6 +50,11 @@ extern "C" {
 #define KSC_ERR_DEVICE_BOUNDS (-5) /* a device-side bounds check fired        */
 #define KSC_ERR_SVD (-6)           /* the split's SVD did not converge        */
 #define KSC_ERR_UNSUPPORTED (-7)   /* valid request this build cannot serve   */
+#define KSC_ERR_TIMEOUT_UNDRAINED (-8) /* a bounded wait ran out and copies or
+                                      MMAs then in flight did not complete within
+                                      the drain's own limit: the kernel's shared
+                                      or tensor memory was released (or, for
+                                      tensor memory, kept) with them pending   */
 
 /* ---- split construction (Sec. 2, Eq. 1-6) ------------------------------ */
 #define KSC_SPLIT_LSQ 0   /* weighted least-squares split, Eq. 3-5 (default) */
@@ -83,12 +88,18 @@ typedef struct {
                           the tensor cores (the belt's tensor form is slower
                           than its circulant FFMA form on GB300)            */
     int cut_continuity; /* LSQ mode: how the fitted real-space kernel meets the
-                          cut (the truncation "to a limit theta_cut" of Sec. 2):
-                          KSC_CUT_C1 (0, default) value and slope vanish at
-                          theta_cut; KSC_CUT_C0 value only; KSC_CUT_FREE the
-                          fit is unconstrained and K_r may jump at the cut
-                          (a jump leaves a pixel-sum error on smooth maps of
-                          about |K_r(theta_cut)| x boundary pixels)          */
+                          cut.  KSC_CUT_FREE is the paper's fit as printed
+                          (Sec. 2, Eq. 3-5: K_r truncated at theta_cut, free
+                          to jump there; a jump leaves a pixel-sum error on
+                          smooth maps of about |K_r(theta_cut)| x boundary
+                          pixels).  KSC_CUT_C1 (0, default) and KSC_CUT_C0 are
+                          this library's addition to that fit, not part of
+                          the paper: the fit also makes K_r vanish at
+                          theta_cut, with zero slope (C1) or not (C0), by
+                          eliminating the unknowns nearest the cut.  At the
+                          nside-2048 5' split (l_cut 1024, 240') the C1 cut
+                          gives a fractional rms C_l error of ~5e-6 where the
+                          paper's fit gives ~1e-4                           */
     int exact_weights; /* 0 (default): the cap ring pairs' kernel weights come
                           from a per-ring-pair cubic table in dphi / 2 (cells
                           of at most 2-3 intervals of the K_r table, built per
@@ -116,6 +127,14 @@ typedef struct {
 
 /* Fill *opts with the defaults listed above. */
 int ksc_default_opts(ksc_split_opts *opts);
+
+/*
+ * Host-side fault injection (for tests; no GPU fault is made): with the
+ * environment variable KSC_FAULT=alloc:N, the N-th device allocation of each
+ * split construction (and of the first ksc_conv_real_host call on a split)
+ * fails as if the device were out of memory.  The call returns KSC_ERR_NOMEM
+ * and releases whatever it had allocated.
+ */
 
 /*
  * Fit the split of kernel b_l (l = 0..lmax, host array) for maps of the given
@@ -306,8 +325,10 @@ void ksc_batch_free(ksc_batch *b);
 
 /*
  * End-to-end convenience: host map in, host map out (12 nside^2 floats each),
- * through library-owned device buffers and the split's own stream.
- * Synchronous.  Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_CUDA.
+ * through library-owned device buffers and the split's own stream (both
+ * created by the first call).  Synchronous.  Calls on one split from several
+ * host threads take turns (the buffers are the split's); calls on different
+ * splits run concurrently.  Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_CUDA.
  */
 int ksc_conv_real_host(const ksc_split *s, const float *h_in, float *h_out);
 
@@ -351,21 +372,25 @@ int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw,
  * Synchronize `stream` and report device-side errors raised by earlier calls
  * on this split: KSC_ERR_TIMEOUT when a bounded wait inside a kernel ran out
  * (the kernel stopped early and its output is incomplete),
- * KSC_ERR_DEVICE_BOUNDS when a device-side bounds check fired.  Clears the
- * flag.  KSC_OK otherwise.
+ * KSC_ERR_TIMEOUT_UNDRAINED when, in addition, copies or MMAs then in flight
+ * outlived the kernel's bounded drain, KSC_ERR_DEVICE_BOUNDS when a device-side
+ * check of the kernels' index invariants fired.  The flag is shared by every
+ * stream that uses the split; it is read and cleared in order on `stream`, so
+ * call this where no other work on the split is in flight.  KSC_OK otherwise.
  */
 int ksc_device_status(const ksc_split *s, void *stream);
 
 /*
  * Exercise the bounded-wait failure path on `stream`: one CTA waits on a
  * shared-memory mbarrier that no thread ever arrives on, with the same bounded
- * poll loop as the tensor-core kernels; when the limit runs out (2^22 polls,
- * about 16 s on a GB300) it raises this split's device error flag as a kernel
- * would, and returns.  Nothing hangs or faults: the next ksc_device_status reports
- * KSC_ERR_TIMEOUT and clears the flag, and the context stays usable.
- * Asynchronous; errors: KSC_ERR_ARG, KSC_ERR_CUDA.
+ * poll loop as the kernels; when max_polls tries have run out (max_polls <= 0:
+ * the kernels' own limit, 2^22 tries, about 16 s on a GB300) it raises this
+ * split's device error flag as a kernel would, and returns.  Nothing hangs or
+ * faults: the next ksc_device_status reports KSC_ERR_TIMEOUT and clears the
+ * flag, and the context stays usable.  Asynchronous; errors: KSC_ERR_ARG,
+ * KSC_ERR_CUDA.
  */
-int ksc_probe_wait_timeout(const ksc_split *s, void *stream);
+int ksc_probe_wait_timeout(const ksc_split *s, int max_polls, void *stream);
 
 /*
  * Allocation-free table build (the paper has no counterpart: this serves
@@ -380,12 +405,90 @@ int ksc_probe_wait_timeout(const ksc_split *s, void *stream);
  * is a built-in device array sized for n_intervals <= 8192 (131 kB held on
  * every device that loads the library until exit); larger n_intervals is
  * rejected with KSC_ERR_ARG.  Calls share that array: calls that overlap on
- * the GPU race.  The first call on each device looks up the array's address
- * (not allowed during stream capture): make it before any capture.
+ * the GPU race.  A call made outside stream capture looks up the array's
+ * address (which follows a reset of the device's context); a call made during
+ * capture uses the address of the last call outside capture on that device, so
+ * make one call before any capture (KSC_ERR_ARG otherwise).
  * Errors: KSC_ERR_ARG, KSC_ERR_CUDA, KSC_ERR_UNSUPPORTED (device index > 63).
  */
 int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
                             int n_intervals, float *d_table, void *stream);
+
+/* ---- split planning: cost models and the scan of Sec. 2 ---------------- */
+/*
+ * Cost of the two halves of a split convolution (Sec. 2, Eq. 7-8, refitted for
+ * this library; host arithmetic only):
+ *   t_gpu  = gpu_ms0 + gpu_ms_per_tpair * P * 1e-12,  P = ksc_cost_pairs(nside, theta_cut)
+ *            (the real-space half costs about a fixed amount per in-disc pixel pair;
+ *            the paper's Eq. 7 is linear in theta_cut for its GTX 480 code);
+ *   t_host = host_ms0 + host_ms_eq8 * l_cut^2 l_max / 4096^3
+ *            (Eq. 8's form for the harmonic half; the paper's host_ms_eq8 = 160e3
+ *            on one 2.8 GHz core).
+ */
+typedef struct {
+    double gpu_ms0, gpu_ms_per_tpair;
+    double host_ms0, host_ms_eq8;
+} ksc_cost_model;
+
+/* In-disc pixel pairs of a map, Npix^2 (1 - cos theta_cut) / 2, Npix = 12 nside^2. */
+double ksc_cost_pairs(int nside, double theta_cut);
+/* GPU: this library on one GB300 (the nside-2048 benchmark: 259 ms for
+ * 3.09e12 pairs); host: Eq. 8 as printed.  Refit both for the machine at hand. */
+int ksc_cost_model_default(ksc_cost_model *m);
+/* t_gpu and t_host (ms) of one split (l_cut < 0: no harmonic half, t_host = 0);
+ * either output may be NULL. */
+int ksc_cost_eval(const ksc_cost_model *m, int nside, int l_cut, int lmax,
+                  double theta_cut, double *t_gpu_ms, double *t_host_ms);
+/* Least-squares fits (in relative error, overhead >= 0) of the GPU terms to n >= 2
+ * measured real-space convolution times, and of the host terms to n >= 2 measured
+ * harmonic-half times; each updates only its own half of *m.  KSC_ERR_ARG for
+ * non-positive times or degenerate data. */
+int ksc_cost_fit_gpu(const int *nside, const double *theta_cut, const double *t_ms,
+                     int n, ksc_cost_model *m);
+int ksc_cost_fit_host(const int *l_cut, const int *lmax, const double *t_ms, int n,
+                      ksc_cost_model *m);
+
+/* The surrogate's inputs for n splits: x[i] = (log2 nside, ln FWHM[rad],
+ * ln l_cut, ln theta_cut[rad]) as floats (x: n x 4, host).  KSC_ERR_ARG for
+ * non-positive inputs. */
+int ksc_split_features(int n, const int *nside, const double *fwhm,
+                       const int *l_cut, const double *theta_cut, float *x);
+
+typedef struct {
+    double theta_lo, theta_hi, theta_step; /* radians; default 30' .. 600' in 30'
+                                              steps (Table 1's cuts are multiples
+                                              of 30')                          */
+    double bound;      /* Eq. 6 bound on the fractional error; default 1e-5      */
+    int l_cut_fixed;   /* -1 (default): binary search for l_cut per theta_cut;
+                          >= 0: only theta_cut is scanned, at this l_cut        */
+} ksc_scan_opts;
+
+typedef struct {
+    double theta_cut;  /* radians                                               */
+    int l_cut;         /* smallest l_cut meeting the bound, or -1 if none       */
+    double error;      /* Eq. 6 at (l_cut, theta_cut); with no l_cut meeting the
+                          bound: at l_max - 1 (or at l_cut_fixed)              */
+    double t_gpu_ms, t_host_ms; /* the cost model at that split                 */
+} ksc_scan_row;
+
+int ksc_scan_default_opts(ksc_scan_opts *o);
+/*
+ * Sec. 2's scanning strategy for kernel b_l (l = 0..lmax) on maps of nside: for
+ * each theta_cut of the grid, a binary search for the smallest l_cut whose
+ * least-squares split (fitted as ksc_make_split does, with split_opts; NULL =
+ * defaults) meets bound in Eq. 6 (with split_opts->alpha; the search takes the
+ * error as falling with l_cut, as Sec. 2 does); then the candidate of least
+ * max(t_gpu, t_host) under `cost` (NULL = ksc_cost_model_default), the two halves
+ * running concurrently (Fig. 1).  rows (max_rows entries, may be NULL) receives
+ * one row per theta_cut, *n_rows their number, *best the index of the chosen row
+ * (-1: no split meets the bound, or it did not fit in rows).  Host FP64 only
+ * (no GPU); synchronous; about one split fit per binary-search step.
+ * Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_SVD.
+ */
+int ksc_scan_split(const double *b_l, int lmax, int nside, const double *cl_in,
+                   const ksc_scan_opts *scan, const ksc_cost_model *cost,
+                   const ksc_split_opts *split_opts, ksc_scan_row *rows,
+                   int max_rows, int *n_rows, int *best);
 
 /* ---- surrogate split selector (learned error / cost model) ------------ */
 /*
@@ -435,8 +538,10 @@ int ksc_mlp_train(ksc_mlp *m, const float *d_x, const float *d_t, int n,
  * log10 eps_C <= log10_bound - margin, or -1 if none.  The cost of a
  * candidate is max(predicted GPU time, h_host_ms[i]) -- the two halves of the
  * split run concurrently (Fig. 1) -- with h_host_ms (may be NULL: GPU time
- * only) the caller's host cost of its harmonic half in ms (e.g. Eq. 8's
- * l_cut^2 l_max model on the caller's host).  h_pred (may be NULL) receives
+ * only) the host cost of its harmonic half in ms (e.g. ksc_cost_eval's t_host
+ * for the caller's host).  When it returns -1 the caller falls back to the
+ * scan (ksc_scan_split), and a measured run of the chosen split decides.
+ * h_pred (may be NULL) receives
  * the n x 2 predictions.  Synchronous. */
 int ksc_mlp_select(const ksc_mlp *m, const float *h_x, int n, double log10_bound,
                    double margin, const double *h_host_ms, int *best, float *h_pred);

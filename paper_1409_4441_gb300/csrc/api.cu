@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -15,14 +16,14 @@ namespace {
 
 // One CTA waits on an mbarrier nothing arrives on (phase 0 never completes); the
 // bounded wait runs out and the CTA raises the error flag like a kernel would.
-__global__ void wait_probe_kernel(int *err) {
+__global__ void wait_probe_kernel(int *err, int max_polls) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         ksc::tc::mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const bool done = ksc::tc::mbar_wait(&bar, 0u);
+    const bool done = ksc::tc::mbar_wait(&bar, 0u, max_polls);
     if (!done && threadIdx.x == 0) atomicExch(err, KSC_ERR_TIMEOUT);
 }
 
@@ -34,7 +35,8 @@ int fail(int code, const std::string &msg) {
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
-    return fail(KSC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? KSC_ERR_NOMEM : KSC_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 constexpr double kPi = 3.14159265358979323846;
@@ -43,9 +45,17 @@ bool valid_nside(int nside) {
     return nside >= 1 && nside <= 8192 && (nside & (nside - 1)) == 0;
 }
 
+// Device allocations of one split construction, counted for fault injection.
+thread_local int g_alloc_count = 0;
+
+cudaError_t dev_malloc(void **dst, size_t bytes) {
+    if (ksc::inject_alloc_fault(++g_alloc_count)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(dst, bytes);
+}
+
 template <class T>
 cudaError_t dev_upload(T **dst, const T *src, size_t n) {
-    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * (n ? n : 1));
+    cudaError_t e = dev_malloc((void **)dst, sizeof(T) * (n ? n : 1));
     if (e != cudaSuccess) return e;
     if (n) e = cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
     return e;
@@ -76,6 +86,7 @@ void release(ksc_split *s) {
 // Geometry, work list and device table for the real-space part s->c_real.
 int finish_split(ksc_split *s, const ksc_split_opts &o) {
     const int nside = s->nside;
+    g_alloc_count = 0;
     s->chord_cut = 2.0 * std::sin(0.5 * s->theta_cut);
     int n_int = o.n_intervals;
     // ~96 intervals per shortest l_max wavelength; the chord compresses
@@ -330,7 +341,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         return cuda_fail(e, "upload work list");
     if ((e = dev_upload(&s->d_items_mma, items_mma.data(), items_mma.size())) != cudaSuccess)
         return cuda_fail(e, "upload work list");
-    if ((e = cudaMalloc(&s->d_err, sizeof(int))) != cudaSuccess)
+    if ((e = dev_malloc((void **)&s->d_err, sizeof(int))) != cudaSuccess)
         return cuda_fail(e, "error flag");
     if ((e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess)
         return cuda_fail(e, "error flag");
@@ -339,11 +350,11 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     double *d_c = nullptr, *d_nodes = nullptr;
     if ((e = dev_upload(&d_c, s->c_real.data(), s->c_real.size())) != cudaSuccess)
         return cuda_fail(e, "upload coefficients");
-    if ((e = cudaMalloc(&d_nodes, sizeof(double) * 2 * (n_int + 1))) != cudaSuccess) {
+    if ((e = dev_malloc((void **)&d_nodes, sizeof(double) * 2 * (n_int + 1))) != cudaSuccess) {
         cudaFree(d_c);
         return cuda_fail(e, "allocate table nodes");
     }
-    if ((e = cudaMalloc(&s->d_tab, sizeof(float4) * (n_int + 1))) != cudaSuccess) {
+    if ((e = dev_malloc((void **)&s->d_tab, sizeof(float4) * (n_int + 1))) != cudaSuccess) {
         cudaFree(d_c); cudaFree(d_nodes);
         return cuda_fail(e, "allocate table");
     }
@@ -463,7 +474,7 @@ cudaError_t launch_caps(const ksc_split *s, const float *d_in, float *d_out, int
     const int c = s->ring_first_sym[lo], d = s->ring_first_sym[hi + 1];
     const ksc::WorkItem *its = whole ? s->d_items_sym_lpt : s->d_items_sym + c;
     return ksc::launch_conv_sym(s->plan, its, d - c, d_in, d_out, n_maps, stride, belt_split,
-                                r0, r1, st);
+                                r0, r1, s->d_err, st);
 }
 
 // The real-space convolution of output rings [r0, r1] (0-based, inclusive).
@@ -508,6 +519,12 @@ int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
 
 namespace ksc {
 void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+bool inject_alloc_fault(int n) {
+    const char *f = std::getenv("KSC_FAULT");
+    if (!f || std::strncmp(f, "alloc:", 6) != 0) return false;
+    return n == std::atoi(f + 6);
+}
 
 XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int L, int lq,
                  double scale) {
@@ -741,15 +758,20 @@ int ksc_conv_real_batch(const ksc_split *const *splits, const float *const *d_in
 int ksc_conv_real_host(const ksc_split *cs, const float *h_in, float *h_out) {
     if (!cs || !h_in || !h_out) return fail(KSC_ERR_ARG, "null argument");
     ksc_split *s = const_cast<ksc_split *>(cs);
+    // the split's host-path stream and buffers serve one call at a time
+    std::lock_guard<std::mutex> lk(s->host_mu);
     cudaError_t e;
     const size_t bytes = sizeof(float) * (size_t)s->plan.npix;
+    if (!s->d_io) {
+        g_alloc_count = 0;
+        if ((e = dev_malloc((void **)&s->d_io, 2 * bytes)) != cudaSuccess) {
+            s->d_io = nullptr;
+            return fail(KSC_ERR_NOMEM, "device buffers for the host path");
+        }
+    }
     if (!s->own_stream) {
         if ((e = cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "stream create");
-    }
-    if (!s->d_io) {
-        if ((e = cudaMalloc(&s->d_io, 2 * bytes)) != cudaSuccess)
-            return fail(KSC_ERR_NOMEM, "device buffers for the host path");
     }
     float *din = s->d_io, *dout = s->d_io + s->plan.npix;
     if ((e = cudaMemcpyAsync(din, h_in, bytes, cudaMemcpyHostToDevice, s->own_stream)) != cudaSuccess)
@@ -768,18 +790,25 @@ int ksc_device_status(const ksc_split *s, void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     int flag = 0;
-    if ((e = cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                             (cudaStream_t)stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(e, "error flag read");
     if (flag != 0) {
-        cudaMemset(s->d_err, 0, sizeof(int));
+        // cleared in order on the caller's stream (the flag is shared by every
+        // stream that uses the split: clear it where no call on this split runs)
+        if ((e = cudaMemsetAsync(s->d_err, 0, sizeof(int), (cudaStream_t)stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess)
+            return cuda_fail(e, "error flag clear");
         return fail(flag, "a device-side check fired during an earlier call");
     }
     return KSC_OK;
 }
 
-int ksc_probe_wait_timeout(const ksc_split *s, void *stream) {
+int ksc_probe_wait_timeout(const ksc_split *s, int max_polls, void *stream) {
     if (!s) return fail(KSC_ERR_ARG, "null split");
-    wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(s->d_err);
+    if (max_polls <= 0 || max_polls > ksc::tc::kMaxWait) max_polls = ksc::tc::kMaxWait;
+    wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(s->d_err, max_polls);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "wait probe launch");
     return KSC_OK;
@@ -870,6 +899,7 @@ const char *ksc_status_string(int st) {
     case KSC_ERR_DEVICE_BOUNDS: return "KSC_ERR_DEVICE_BOUNDS";
     case KSC_ERR_SVD: return "KSC_ERR_SVD";
     case KSC_ERR_UNSUPPORTED: return "KSC_ERR_UNSUPPORTED";
+    case KSC_ERR_TIMEOUT_UNDRAINED: return "KSC_ERR_TIMEOUT_UNDRAINED";
     default: return "KSC_ERR_UNKNOWN";
     }
 }

@@ -234,7 +234,8 @@ int enqueue(ksc_batch *b, const std::vector<Launch> &launches, const int4 *d_ite
                                             b->d_counters + i, st);
         else
             e = ksc::launch_conv_sym_batch(L.variant, b->d_plans, b->d_entries, d_items + L.first,
-                                           L.count, b->opts.per_sm_cap, b->d_counters + i, st);
+                                           L.count, b->opts.per_sm_cap, b->d_counters + i,
+                                           b->d_err, st);
         if (e != cudaSuccess) return bcuda(e, "batch kernel launch");
     }
     if (general) {

@@ -233,10 +233,14 @@ __device__ __forceinline__ bool belt_item(const ConvPlan &P, int r, int k0,
     }
     __syncthreads();
     if (*s_abort) {
-        if (tid == 0) atomicExch(err, KSC_ERR_TIMEOUT);
-        // wait (bounded) for any copy still in flight before leaving
-        mbar_wait(&bar[0], phase0);
-        mbar_wait(&bar[1], phase1);
+        // wait (bounded) for any copy still in flight before leaving; a copy that
+        // outlives that wait too is reported as such (it may still write the
+        // buffers of a CTA that has exited)
+        if (tid == 0) {
+            const bool d0 = mbar_wait(&bar[0], phase0);
+            const bool d1 = mbar_wait(&bar[1], phase1);
+            atomicExch(err, d0 && d1 ? KSC_ERR_TIMEOUT : KSC_ERR_TIMEOUT_UNDRAINED);
+        }
         return false;
     }
 #pragma unroll

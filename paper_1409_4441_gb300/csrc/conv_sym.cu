@@ -213,7 +213,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                                          bool skip_belt_inputs, bool add, int band_lo,
                                          int band_hi, const float *__restrict__ m,
                                          float *__restrict__ o, SymRing *sR, float *st,
-                                         float4 *xt) {
+                                         float4 *xt, int *__restrict__ err) {
     constexpr int T = S::T, C = S::C, kSpan = S::kSpan, kStride = S::kStride;
     const int tid = threadIdx.x;
     const DevRing R = P.d_rings[r];
@@ -259,6 +259,12 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             }
             const TabPos x{g.inv, (float)off * g.inv, (float)nct, (float)(2 * L) * g.inv,
                            (float)(2 * L2) * g.inv};
+            // invariants the arithmetic relies on (the host's split construction
+            // guarantees them): class integers fit in int32, and table positions within
+            // a few positions of the cut stay exact in FP32
+            if (tid == 0 && (num0 + 2LL * S::kClasses * L2 > 2147483647LL ||
+                             (use_xt && (long long)g.ncut + 32LL * L >= (1LL << 24))))
+                atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 // positions this segment needs (the union ends at U1)
                 const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
@@ -335,7 +341,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
 template <class S>
 __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0, int belt_split,
                                              int band_lo, int band_hi, const float *m, float *o,
-                                             SymRing *sR, float *st, float4 *xt) {
+                                             SymRing *sR, float *st, float4 *xt, int *err) {
     const int eq = (P.nrings - 1) / 2;  // the equator ring, its own mirror image
     const DevRing R = P.d_rings[ring];
     const int Q = R.len / 4;
@@ -343,9 +349,9 @@ __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0
     const bool belt = ring >= P.belt_lo && ring <= P.belt_hi;
     const bool add = belt_split && belt;
     if (ring == eq)
-        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt);
+        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt, err);
     else
-        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt);
+        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt, err);
 }
 
 // One split; grid.y runs over maps.  CTAs claim items in list order through a
@@ -356,7 +362,8 @@ template <class S>
 __global__ void __launch_bounds__(S::T, S::MINB)
 conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_items,
                 const float *__restrict__ in, float *__restrict__ out, long long map_stride,
-                int belt_split, int band_lo, int band_hi, int *__restrict__ counters) {
+                int belt_split, int band_lo, int band_hi, int *__restrict__ counters,
+                int *__restrict__ err) {
     __shared__ SymRing sR[kRingChunk];
     __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
@@ -370,7 +377,7 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
         const int it = s_next;
         if (it >= n_items) break;
         const WorkItem w = items[it];
-        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st, xt);
+        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st, xt, err);
     }
 }
 
@@ -379,7 +386,8 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
 template <class S>
 __global__ void __launch_bounds__(S::T, S::MINB)
 conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__restrict__ entries,
-                      const int4 *__restrict__ items, int n_items, int *__restrict__ counter) {
+                      const int4 *__restrict__ items, int n_items, int *__restrict__ counter,
+                      int *__restrict__ err) {
     __shared__ SymRing sR[kRingChunk];
     __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
@@ -393,7 +401,8 @@ conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__re
         const int4 w = items[it];
         const BatchEntry e = entries[w.x];
         const ConvPlan &P = plans[e.plan];
-        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st, xt);
+        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st, xt,
+                        err);
     }
 }
 
@@ -430,7 +439,7 @@ cudaError_t sym_grid(K kernel, int threads, size_t dyn_smem, int n_items, int pe
 template <class S>
 cudaError_t sym_launch(const ConvPlan &p, const WorkItem *d_items, int n_items,
                        const float *d_in, float *d_out, int n_maps, long long map_stride,
-                       int belt_split, int band_lo, int band_hi, cudaStream_t st) {
+                       int belt_split, int band_lo, int band_hi, int *d_err, cudaStream_t st) {
     int blocks = 0;
     cudaError_t e = sym_grid(conv_sym_kernel<S>, S::T, S::kDynSmem, n_items, 0, &blocks);
     if (e != cudaSuccess) return e;
@@ -443,7 +452,7 @@ cudaError_t sym_launch(const ConvPlan &p, const WorkItem *d_items, int n_items,
         dim3 grid(blocks, n_maps);
         conv_sym_kernel<S><<<grid, S::T, S::kDynSmem, st>>>(p, d_items, n_items, d_in, d_out,
                                                            map_stride, belt_split, band_lo,
-                                                           band_hi, ctr);
+                                                           band_hi, ctr, d_err);
         e = cudaGetLastError();
     }
     const cudaError_t f = cudaFreeAsync(ctr, st);
@@ -463,13 +472,14 @@ int sym_chunk(int nside) { return nside >= 2048 ? ShapeC3::kClasses : ShapeWide:
 
 cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
                             const float *d_in, float *d_out, int n_maps, long long map_stride,
-                            int belt_split, int band_lo, int band_hi, cudaStream_t st) {
+                            int belt_split, int band_lo, int band_hi, int *d_err,
+                            cudaStream_t st) {
     if (n_items <= 0 || n_maps <= 0) return cudaSuccess;
     if (sym_chunk(p.nside) == ShapeC3::kClasses)
         return sym_launch<ShapeC3>(p, d_items, n_items, d_in, d_out, n_maps, map_stride,
-                                   belt_split, band_lo, band_hi, st);
+                                   belt_split, band_lo, band_hi, d_err, st);
     return sym_launch<ShapeWide>(p, d_items, n_items, d_in, d_out, n_maps, map_stride,
-                                 belt_split, band_lo, band_hi, st);
+                                 belt_split, band_lo, band_hi, d_err, st);
 }
 
 int sym_variants() { return 3; }
@@ -482,28 +492,28 @@ int sym_variant_chunk(int variant) {
 template <class S>
 cudaError_t sym_batch_launch(const ConvPlan *d_plans, const BatchEntry *d_entries,
                              const int4 *d_items, int n_items, int per_sm_cap, int *d_counter,
-                             cudaStream_t st) {
+                             int *d_err, cudaStream_t st) {
     int blocks = 0;
     cudaError_t e =
         sym_grid(conv_sym_batch_kernel<S>, S::T, S::kDynSmem, n_items, per_sm_cap, &blocks);
     if (e != cudaSuccess) return e;
     conv_sym_batch_kernel<S><<<blocks, S::T, S::kDynSmem, st>>>(d_plans, d_entries, d_items,
-                                                                n_items, d_counter);
+                                                                n_items, d_counter, d_err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
                                   const BatchEntry *d_entries, const int4 *d_items, int n_items,
-                                  int per_sm_cap, int *d_counter, cudaStream_t st) {
+                                  int per_sm_cap, int *d_counter, int *d_err, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
     if (variant == 2)
         return sym_batch_launch<ShapeWide>(d_plans, d_entries, d_items, n_items, per_sm_cap,
-                                           d_counter, st);
+                                           d_counter, d_err, st);
     if (variant == 1)
         return sym_batch_launch<ShapeSmall>(d_plans, d_entries, d_items, n_items, per_sm_cap,
-                                            d_counter, st);
+                                            d_counter, d_err, st);
     return sym_batch_launch<ShapeC3>(d_plans, d_entries, d_items, n_items, per_sm_cap,
-                                     d_counter, st);
+                                     d_counter, d_err, st);
 }
 
 } // namespace ksc

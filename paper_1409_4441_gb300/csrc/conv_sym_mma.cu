@@ -208,6 +208,11 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
                     khi = 0;
                 }
                 const bool use_xt = g.ncell > 0 && g.ncell <= kXCap;
+                // invariants the arithmetic relies on (guaranteed by the split's
+                // construction): pixel-pair integers near the window exact in FP32
+                if (tid == 0 && (numx + 2LL * kM * g.len > 2147483647LL ||
+                                 (use_xt && (long long)g.ncut + 32LL * L >= (1LL << 24))))
+                    atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
                 if (use_xt) {  // (the previous ring pair ended at a barrier)
                     xtab_build<kThreads>(P, g, xt);
                     __syncthreads();
@@ -377,6 +382,7 @@ conv_sym_mma_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_
     }
     tc::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && !s_drained) atomicExch(err, KSC_ERR_TIMEOUT_UNDRAINED);
     if (warp == 0 && s_drained)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));

@@ -298,6 +298,12 @@ conv_sym_tc_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_i
                 const int nct = (g.ncut + 1 + off) >> g.shift;
                 const bool use_xt = g.ncell > 0 && nct + 1 <= kXCap;
                 const float offS = (float)off * g.inv, ncf = (float)nct;
+                // invariants the arithmetic relies on (guaranteed by the split's
+                // construction): class integers fit in int32, and table positions within
+                // a step of the cut stay exact in FP32
+                if (tid == 0 && (numx + 2LL * kM * g.len > 2147483647LL ||
+                                 (use_xt && (long long)g.ncut + 32LL * L >= (1LL << 24))))
+                    atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
                 int wa = klo, wb = khi;
                 if (use_xt) {  // the class's positions within the cut
                     wa = max(klo, ceil_div(num - g.ncut, 2 * L));
@@ -487,6 +493,7 @@ conv_sym_tc_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_i
     }
     tc::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && !s_drained) atomicExch(err, KSC_ERR_TIMEOUT_UNDRAINED);
     if (warp == 4 && s_drained)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));

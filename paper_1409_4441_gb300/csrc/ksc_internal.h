@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -174,7 +175,7 @@ int sym_classes(int len, int phase);  // reflection classes of a ring's first qu
 cudaError_t launch_conv_sym(const ConvPlan &p, const WorkItem *d_items, int n_items,
                             const float *d_in, float *d_out, int n_maps,
                             long long map_stride, int belt_split, int band_lo,
-                            int band_hi, cudaStream_t st);
+                            int band_hi, int *d_err, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Batched persistent launches (csrc/batch.cpp).  An entry is one map convolved
@@ -200,7 +201,7 @@ cudaError_t launch_conv_belt_batch(int variant, const ConvPlan *d_plans,
                                    cudaStream_t st);
 cudaError_t launch_conv_sym_batch(int variant, const ConvPlan *d_plans,
                                   const BatchEntry *d_entries, const int4 *d_items, int n_items,
-                                  int per_sm_cap, int *d_counter, cudaStream_t st);
+                                  int per_sm_cap, int *d_counter, int *d_err, cudaStream_t st);
 
 // tcgen05 gather for map stacks (symmetric ring pairs): items are the
 // symmetric work items of sym_mma_chunk() classes each; maps in groups of
@@ -223,6 +224,12 @@ cudaError_t launch_conv_sym_mma(const ConvPlan &p, const WorkItem *d_items, int 
 
 // Record the message returned by ksc_last_error() on this thread.
 void set_last_error(const std::string &msg);
+
+// Host-side fault injection for tests (no GPU fault is ever made): the
+// environment variable KSC_FAULT = "alloc:N" makes the N-th device allocation of
+// each split construction or host-path call fail as if the device were out of
+// memory (N >= 1).  Returns true when allocation number `n` (1-based) must fail.
+bool inject_alloc_fault(int n);
 
 // Largest table (intervals) a convolution kernel keeps in shared memory.
 constexpr int kMaxIntervals = 8192;
@@ -276,7 +283,8 @@ struct ksc_split {
     int *d_err = nullptr;                  // device error flag (bounded waits)
     ksc::ConvPlan plan{};
 
-    // end-to-end host path
+    // end-to-end host path (one call at a time per split: host_mu)
+    std::mutex host_mu;
     cudaStream_t own_stream = nullptr;
     float *d_io = nullptr;  // 2 * npix floats, allocated on first host call
 };

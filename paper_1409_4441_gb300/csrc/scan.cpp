@@ -1,0 +1,234 @@
+// Split planning on the host (declared in include/ksconv.h): the cost models of
+// the two halves of the split convolution (Sec. 2, Eq. 7-8 refitted for this
+// library), the surrogate's input features, and the scanning strategy of Sec. 2
+// that picks the cheapest (l_cut, theta_cut) meeting an error bound.
+//
+// Cost models.  The GPU half (the real-space sum) costs about a fixed amount
+// per in-disc pixel pair, t_gpu = g0 + g1 P(nside, theta_cut) with P the pair
+// count of a disc of radius theta_cut on a map of Npix pixels,
+// P = Npix^2 (1 - cos theta_cut) / 2 (the paper's Eq. 7 is linear in theta_cut
+// for its GTX 480 code, whose cost per ring pair dominated).  The host half (an
+// SHT to l_cut on a map with l_max) follows Eq. 8, t_host = h0 + h1 l_cut^2 l_max
+// / 4096^3 (the paper's h1 = 160 s for one 2.8 GHz core).  Both are fitted by
+// least squares in relative error to measured times.
+//
+// Scan (Sec. 2): a linear scan over theta_cut on a grid; for each theta_cut a
+// binary search for the smallest l_cut whose fitted split meets the Eq. 6 bound
+// (the error is taken as falling with l_cut, as Sec. 2 does; where it does not,
+// the search returns one l_cut meeting the bound); the candidate of least
+// max(t_gpu, t_host) wins -- the two halves run concurrently (Fig. 1).
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "ksc_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kArcmin = kPi / (180.0 * 60.0);
+
+int sfail(int code, const std::string &msg) {
+    ksc::set_last_error(msg);
+    return code;
+}
+
+// least squares of t_i ~ a0 + a1 x_i in relative error: minimise
+// sum ((a0 + a1 x_i) / t_i - 1)^2 (a 2 x 2 normal system); a0 >= 0
+bool fit_rel(const std::vector<double> &x, const std::vector<double> &t, double *a0, double *a1) {
+    double s00 = 0, s01 = 0, s11 = 0, r0 = 0, r1 = 0;
+    for (size_t i = 0; i < x.size(); ++i) {
+        const double u = 1.0 / t[i], v = x[i] / t[i];
+        s00 += u * u; s01 += u * v; s11 += v * v; r0 += u; r1 += v;
+    }
+    const double det = s00 * s11 - s01 * s01;
+    if (!(std::fabs(det) > 1e-300 * std::max(1.0, s00 * s11))) return false;
+    *a0 = (r0 * s11 - r1 * s01) / det;
+    *a1 = (s00 * r1 - s01 * r0) / det;
+    if (*a0 < 0.0) {  // a negative overhead: fit the slope alone
+        *a0 = 0.0;
+        if (!(s11 > 0.0)) return false;
+        *a1 = r1 / s11;
+    }
+    return std::isfinite(*a0) && std::isfinite(*a1);
+}
+
+double eq8_units(int l_cut, int lmax) {
+    return (double)l_cut * (double)l_cut * (double)lmax / (4096.0 * 4096.0 * 4096.0);
+}
+
+} // namespace
+
+extern "C" {
+
+double ksc_cost_pairs(int nside, double theta_cut) {
+    const double npix = 12.0 * (double)nside * (double)nside;
+    const double th = std::min(std::max(theta_cut, 0.0), kPi);
+    return npix * npix * 0.5 * (1.0 - std::cos(th));
+}
+
+int ksc_cost_model_default(ksc_cost_model *m) {
+    if (!m) return sfail(KSC_ERR_ARG, "null model");
+    // GPU: this library on one GB300 -- the nside-2048 benchmark (3.09e12 pairs,
+    // 259 ms per map); host: Eq. 8 as printed (160 s on one 2.8 GHz core)
+    m->gpu_ms0 = 0.1;
+    m->gpu_ms_per_tpair = 259.0 / 3.085;
+    m->host_ms0 = 0.0;
+    m->host_ms_eq8 = 160.0e3;
+    return KSC_OK;
+}
+
+int ksc_cost_eval(const ksc_cost_model *m, int nside, int l_cut, int lmax, double theta_cut,
+                  double *t_gpu_ms, double *t_host_ms) {
+    if (!m) return sfail(KSC_ERR_ARG, "null model");
+    if (t_gpu_ms)
+        *t_gpu_ms = m->gpu_ms0 + m->gpu_ms_per_tpair * ksc_cost_pairs(nside, theta_cut) * 1e-12;
+    if (t_host_ms)
+        *t_host_ms = l_cut < 0 ? 0.0 : m->host_ms0 + m->host_ms_eq8 * eq8_units(l_cut, lmax);
+    return KSC_OK;
+}
+
+int ksc_cost_fit_gpu(const int *nside, const double *theta_cut, const double *t_ms, int n,
+                     ksc_cost_model *m) {
+    if (!nside || !theta_cut || !t_ms || !m || n < 2) return sfail(KSC_ERR_ARG, "bad fit data");
+    std::vector<double> x, t;
+    for (int i = 0; i < n; ++i) {
+        if (!(t_ms[i] > 0.0) || nside[i] < 1) return sfail(KSC_ERR_ARG, "bad fit sample");
+        x.push_back(ksc_cost_pairs(nside[i], theta_cut[i]) * 1e-12);
+        t.push_back(t_ms[i]);
+    }
+    double a0, a1;
+    if (!fit_rel(x, t, &a0, &a1)) return sfail(KSC_ERR_ARG, "degenerate fit data");
+    m->gpu_ms0 = a0;
+    m->gpu_ms_per_tpair = a1;
+    return KSC_OK;
+}
+
+int ksc_cost_fit_host(const int *l_cut, const int *lmax, const double *t_ms, int n,
+                      ksc_cost_model *m) {
+    if (!l_cut || !lmax || !t_ms || !m || n < 2) return sfail(KSC_ERR_ARG, "bad fit data");
+    std::vector<double> x, t;
+    for (int i = 0; i < n; ++i) {
+        if (!(t_ms[i] > 0.0) || l_cut[i] < 0 || lmax[i] < 1)
+            return sfail(KSC_ERR_ARG, "bad fit sample");
+        x.push_back(eq8_units(l_cut[i], lmax[i]));
+        t.push_back(t_ms[i]);
+    }
+    double a0, a1;
+    if (!fit_rel(x, t, &a0, &a1)) return sfail(KSC_ERR_ARG, "degenerate fit data");
+    m->host_ms0 = a0;
+    m->host_ms_eq8 = a1;
+    return KSC_OK;
+}
+
+int ksc_split_features(int n, const int *nside, const double *fwhm, const int *l_cut,
+                       const double *theta_cut, float *x) {
+    if (n < 0 || (n > 0 && (!nside || !fwhm || !l_cut || !theta_cut || !x)))
+        return sfail(KSC_ERR_ARG, "bad feature arrays");
+    for (int i = 0; i < n; ++i) {
+        if (nside[i] < 1 || !(fwhm[i] > 0.0) || l_cut[i] < 1 || !(theta_cut[i] > 0.0))
+            return sfail(KSC_ERR_ARG, "feature inputs must be positive");
+        x[4 * i + 0] = (float)std::log2((double)nside[i]);
+        x[4 * i + 1] = (float)std::log(fwhm[i]);
+        x[4 * i + 2] = (float)std::log((double)l_cut[i]);
+        x[4 * i + 3] = (float)std::log(theta_cut[i]);
+    }
+    return KSC_OK;
+}
+
+int ksc_scan_default_opts(ksc_scan_opts *o) {
+    if (!o) return sfail(KSC_ERR_ARG, "null opts");
+    o->theta_lo = 30.0 * kArcmin;
+    o->theta_hi = 600.0 * kArcmin;
+    o->theta_step = 30.0 * kArcmin;
+    o->bound = 1e-5;
+    o->l_cut_fixed = -1;
+    return KSC_OK;
+}
+
+int ksc_scan_split(const double *b_l, int lmax, int nside, const double *cl_in,
+                   const ksc_scan_opts *sopts, const ksc_cost_model *cost,
+                   const ksc_split_opts *opts, ksc_scan_row *rows, int max_rows, int *n_rows,
+                   int *best) {
+    if (!b_l || !n_rows || !best) return sfail(KSC_ERR_ARG, "null argument");
+    if (lmax < 2 || lmax > 16384) return sfail(KSC_ERR_ARG, "lmax outside 2..16384");
+    if (nside < 1 || nside > 8192) return sfail(KSC_ERR_ARG, "nside outside 1..8192");
+    ksc_scan_opts so;
+    ksc_scan_default_opts(&so);
+    if (sopts) so = *sopts;
+    if (!(so.theta_step > 0.0) || !(so.theta_lo > 0.0) || so.theta_hi < so.theta_lo ||
+        so.theta_hi > kPi || !(so.bound > 0.0) || so.l_cut_fixed >= lmax)
+        return sfail(KSC_ERR_ARG, "bad scan options");
+    ksc_cost_model cm;
+    ksc_cost_model_default(&cm);
+    if (cost) cm = *cost;
+    ksc_split_opts o;
+    ksc_default_opts(&o);
+    if (opts) o = *opts;
+    const int oversample = o.oversample > 0 ? o.oversample : 2;
+    const double rcond = o.svd_rcond > 0.0 ? o.svd_rcond : 1e-6;
+    const double alpha = o.alpha > 0.0 ? o.alpha : 5.0;
+    const int n_con = o.cut_continuity == KSC_CUT_FREE ? 0
+                      : (o.cut_continuity == KSC_CUT_C0 ? 1 : 2);
+    const int n_theta = (int)std::floor((so.theta_hi - so.theta_lo) / so.theta_step + 1e-9) + 1;
+    *n_rows = 0;
+    *best = -1;
+    std::string msg;
+    int rc = KSC_OK;
+    // Eq. 6 of the split fitted at (l_cut, theta); < 0 when the fit fails
+    auto err = [&](int lc, double th) -> double {
+        ksc::FitResult fr;
+        const int r = ksc::fit_split_lsq(b_l, lmax, lc, th, cl_in, oversample, rcond, n_con,
+                                         &fr, &msg);
+        if (r) { rc = r; return -1.0; }
+        return ksc::frac_error_eq6(b_l, fr.k_tilde.data(), cl_in, lmax, alpha);
+    };
+    double best_cost = 0.0;
+    try {
+        for (int it = 0; it < n_theta; ++it) {
+            const double th = so.theta_lo + it * so.theta_step;
+            ksc_scan_row row{th, -1, 0.0, 0.0, 0.0};
+            if (so.l_cut_fixed >= 0) {
+                row.error = err(so.l_cut_fixed, th);
+                if (rc) break;
+                if (row.error <= so.bound) row.l_cut = so.l_cut_fixed;
+            } else {
+                int lo = 0, hi = lmax - 1;
+                const double e_hi = err(hi, th);
+                if (rc) break;
+                row.error = e_hi;
+                if (e_hi <= so.bound) {
+                    while (lo < hi) {  // smallest l_cut meeting the bound
+                        const int mid = (lo + hi) / 2;
+                        const double e = err(mid, th);
+                        if (rc) break;
+                        if (e <= so.bound) hi = mid; else lo = mid + 1;
+                    }
+                    if (rc) break;
+                    row.l_cut = lo;
+                    row.error = err(lo, th);
+                    if (rc) break;
+                }
+            }
+            const int lc = so.l_cut_fixed >= 0 ? so.l_cut_fixed : row.l_cut;
+            ksc_cost_eval(&cm, nside, lc, lmax, th, &row.t_gpu_ms, &row.t_host_ms);
+            if (row.l_cut >= 0) {
+                const double c = std::max(row.t_gpu_ms, row.t_host_ms);
+                if (*best < 0 || c < best_cost) {
+                    *best = *n_rows;
+                    best_cost = c;
+                }
+            }
+            if (rows && *n_rows < max_rows) rows[*n_rows] = row;
+            ++*n_rows;
+        }
+    } catch (const std::bad_alloc &) {
+        return sfail(KSC_ERR_NOMEM, "host allocation in the scan");
+    }
+    if (rc) return sfail(rc, msg);
+    if (*best >= max_rows) *best = -1;  // (the caller's rows array was too short)
+    return KSC_OK;
+}
+
+} // extern "C"

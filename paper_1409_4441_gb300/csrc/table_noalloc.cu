@@ -14,9 +14,12 @@
 // overwrites every scratch value it reads, so nothing needs clearing between
 // calls; but all calls share the one array, so calls that overlap on the GPU
 // (different streams, no ordering between them) race and may corrupt each
-// other's tables.  The first call on a device looks up the array's device
-// address (cudaGetSymbolAddress, a set-up step that must not run during
-// stream capture); make that first call before any capture.
+// other's tables.  A call made outside stream capture looks up the array's
+// device address (cudaGetSymbolAddress, which must not run during capture) and
+// remembers it for the device, so the address follows a reset of the device's
+// context; a call made while its stream is being captured uses the address
+// remembered by the last call outside capture on that device, so make one call
+// before any capture (and again after a device reset).
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -60,14 +63,21 @@ int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut, int n
     if (dev < 0 || dev >= kMaxDevices) return fail(KSC_ERR_UNSUPPORTED, "device index above 63");
     double *scratch = nullptr;
     {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const bool capturing =
+            cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess ||
+            cs != cudaStreamCaptureStatusNone;
+        if (capturing) (void)cudaGetLastError();  // (an illegal query during capture)
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        if (!capturing) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_table_scratch);
             if (e != cudaSuccess)
                 return fail(KSC_ERR_CUDA,
                             std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             g_scratch_ptr[dev] = static_cast<double *>(p);
+        } else if (!g_scratch_ptr[dev]) {
+            return fail(KSC_ERR_ARG, "first call on this device made during stream capture");
         }
         scratch = g_scratch_ptr[dev];
     }

@@ -29,6 +29,7 @@ KSC_ERR_TIMEOUT = -4
 KSC_ERR_DEVICE_BOUNDS = -5
 KSC_ERR_SVD = -6
 KSC_ERR_UNSUPPORTED = -7
+KSC_ERR_TIMEOUT_UNDRAINED = -8
 MODES = {"lsq": 0, "sharp": 1, "none": 2}
 KSC_CUT_C1 = 0    # default: the real-space kernel's value and slope vanish at theta_cut
 KSC_CUT_C0 = 1    # value only
@@ -47,6 +48,8 @@ EXPORTS = [
     "ksc_mlp_n_params", "ksc_mlp_create", "ksc_mlp_set_norm", "ksc_mlp_get_params",
     "ksc_mlp_set_params", "ksc_mlp_predict", "ksc_mlp_grad", "ksc_mlp_train", "ksc_mlp_select",
     "ksc_mlp_free",
+    "ksc_cost_pairs", "ksc_cost_model_default", "ksc_cost_eval", "ksc_cost_fit_gpu",
+    "ksc_cost_fit_host", "ksc_split_features", "ksc_scan_default_opts", "ksc_scan_split",
     "ksc_status_string", "ksc_last_error",
 ]
 
@@ -88,6 +91,23 @@ class BatchDesc(ctypes.Structure):
                 ("group_sym_variant", ctypes.c_int * 8)]
 
 
+class CostModel(ctypes.Structure):
+    _fields_ = [("gpu_ms0", ctypes.c_double), ("gpu_ms_per_tpair", ctypes.c_double),
+                ("host_ms0", ctypes.c_double), ("host_ms_eq8", ctypes.c_double)]
+
+
+class ScanOpts(ctypes.Structure):
+    _fields_ = [("theta_lo", ctypes.c_double), ("theta_hi", ctypes.c_double),
+                ("theta_step", ctypes.c_double), ("bound", ctypes.c_double),
+                ("l_cut_fixed", ctypes.c_int)]
+
+
+class ScanRow(ctypes.Structure):
+    _fields_ = [("theta_cut", ctypes.c_double), ("l_cut", ctypes.c_int),
+                ("error", ctypes.c_double), ("t_gpu_ms", ctypes.c_double),
+                ("t_host_ms", ctypes.c_double)]
+
+
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 _sig = {
     "ksc_default_opts": [ctypes.POINTER(Opts)],
@@ -107,7 +127,7 @@ _sig = {
     "ksc_conv_real_multimap_stage": [_vp, _vp, _vp, _i, _i, _vp],
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
     "ksc_dphi_table_params": [_d, _d, _d, _i, _d, _i, _d, _vp],
-    "ksc_probe_wait_timeout": [_vp, _vp],
+    "ksc_probe_wait_timeout": [_vp, ctypes.c_int, _vp],
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
     "ksc_build_table_noalloc": [_vp, _i, _d, _i, _vp, _vp],
@@ -128,6 +148,14 @@ _sig = {
     "ksc_mlp_train": [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp],
     "ksc_mlp_select": [_vp, _vp, _i, _d, _d, _vp, ctypes.POINTER(_i), _vp],
     "ksc_mlp_free": [_vp],
+    "ksc_cost_model_default": [ctypes.POINTER(CostModel)],
+    "ksc_cost_eval": [ctypes.POINTER(CostModel), _i, _i, _i, _d, _vp, _vp],
+    "ksc_cost_fit_gpu": [_vp, _vp, _vp, _i, ctypes.POINTER(CostModel)],
+    "ksc_cost_fit_host": [_vp, _vp, _vp, _i, ctypes.POINTER(CostModel)],
+    "ksc_split_features": [_i, _vp, _vp, _vp, _vp, _vp],
+    "ksc_scan_default_opts": [ctypes.POINTER(ScanOpts)],
+    "ksc_scan_split": [_vp, _i, _i, _vp, ctypes.POINTER(ScanOpts), ctypes.POINTER(CostModel),
+                       ctypes.POINTER(Opts), _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)],
     "ksc_status_string": [_i],
     "ksc_last_error": [],
 }
@@ -136,6 +164,8 @@ for _name, _args in _sig.items():
     _f.argtypes = _args
     _f.restype = _i
 _lib.ksc_free_split.restype = None
+_lib.ksc_cost_pairs.argtypes = [_i, _d]
+_lib.ksc_cost_pairs.restype = _d
 _lib.ksc_batch_free.restype = None
 _lib.ksc_mlp_free.restype = None
 _lib.ksc_status_string.restype = ctypes.c_char_p
@@ -287,10 +317,10 @@ def dphi_table_params(A2: float, B2: float, c: float, n_int: int, hw: float, lq:
     return {"dx": float(out[0]), "ncell": int(out[1]), "ncut": float(out[2])}
 
 
-def probe_wait_timeout(s: Split, stream=None):
-    """Run one bounded wait that nothing completes; the next device_status raises
-    KSC_ERR_TIMEOUT (and clears it)."""
-    _check(_lib.ksc_probe_wait_timeout(s.handle, _stream(stream)), "ksc_probe_wait_timeout")
+def probe_wait_timeout(s: Split, max_polls: int = 0, stream=None):
+    """Run the bounded-wait failure path once (max_polls <= 0: the kernels' limit)."""
+    _check(_lib.ksc_probe_wait_timeout(s.handle, int(max_polls), _stream(stream)),
+           "ksc_probe_wait_timeout")
 
 
 def device_status(s: Split, stream=None):
@@ -531,14 +561,92 @@ class MLP:
         self.close()
 
 
-def harmonic_cost_eq8_ms(l_cut, l_max, cores: int = 1):
-    """Eq. 8's host cost of the harmonic half, 160 s l_cut^2 l_max / 4096^3 (the paper's
-    single 2.8 GHz Core2 core running libpsht), spread over `cores` cores, in ms."""
-    return 160e3 * np.asarray(l_cut, float) ** 2 * np.asarray(l_max, float) / 4096.0 ** 3 / cores
+def cost_model(**fields) -> CostModel:
+    """The library's default cost model (ksc_cost_model_default), fields overridden."""
+    m = CostModel()
+    _check(_lib.ksc_cost_model_default(ctypes.byref(m)), "ksc_cost_model_default")
+    for k, v in fields.items():
+        setattr(m, k, float(v))
+    return m
+
+
+def eq8_cost_model(cores: int = 1) -> CostModel:
+    """The host half as Eq. 8 prints it (160 s l_cut^2 l_max / 4096^3 on one 2.8 GHz
+    core), spread over `cores` cores."""
+    return cost_model(host_ms0=0.0, host_ms_eq8=160e3 / cores)
+
+
+def cost_pairs(nside: int, theta_cut: float) -> float:
+    return float(_lib.ksc_cost_pairs(int(nside), float(theta_cut)))
+
+
+def cost_eval(m: CostModel, nside: int, l_cut: int, lmax: int, theta_cut: float):
+    """(t_gpu_ms, t_host_ms) of one split under model m."""
+    g, h = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.ksc_cost_eval(ctypes.byref(m), int(nside), int(l_cut), int(lmax),
+                              float(theta_cut), ctypes.byref(g), ctypes.byref(h)),
+           "ksc_cost_eval")
+    return g.value, h.value
+
+
+def host_cost_ms(m: CostModel, l_cut, lmax) -> np.ndarray:
+    """t_host (ms) for arrays of l_cut and l_max under model m."""
+    lc, lm = np.broadcast_arrays(np.asarray(l_cut), np.asarray(lmax))
+    return np.array([cost_eval(m, 1, int(a), int(b), 1e-3)[1] for a, b in zip(lc.ravel(),
+                                                                             lm.ravel())])
+
+
+def cost_fit_gpu(m: CostModel, nside, theta_cut, t_ms) -> CostModel:
+    ns = np.ascontiguousarray(nside, dtype=np.int32)
+    th = np.ascontiguousarray(theta_cut, dtype=np.float64)
+    t = np.ascontiguousarray(t_ms, dtype=np.float64)
+    _check(_lib.ksc_cost_fit_gpu(ns.ctypes.data, th.ctypes.data, t.ctypes.data, ns.size,
+                                 ctypes.byref(m)), "ksc_cost_fit_gpu")
+    return m
+
+
+def cost_fit_host(m: CostModel, l_cut, lmax, t_ms) -> CostModel:
+    lc = np.ascontiguousarray(l_cut, dtype=np.int32)
+    lm = np.ascontiguousarray(lmax, dtype=np.int32)
+    t = np.ascontiguousarray(t_ms, dtype=np.float64)
+    _check(_lib.ksc_cost_fit_host(lc.ctypes.data, lm.ctypes.data, t.ctypes.data, lc.size,
+                                  ctypes.byref(m)), "ksc_cost_fit_host")
+    return m
 
 
 def split_features(nside, fwhm_rad, l_cut, theta_cut_rad) -> np.ndarray:
-    """Surrogate inputs (log2 nside, ln FWHM, ln l_cut, ln theta_cut), float32 (n, 4)."""
-    nside, fwhm, lc, tc = (np.atleast_1d(np.asarray(v, dtype=np.float64))
-                           for v in (nside, fwhm_rad, l_cut, theta_cut_rad))
-    return np.stack([np.log2(nside), np.log(fwhm), np.log(lc), np.log(tc)], axis=1).astype(np.float32)
+    """Surrogate inputs (ksc_split_features), float32 (n, 4)."""
+    ns, fw, lc, tc = np.broadcast_arrays(*(np.atleast_1d(np.asarray(v)) for v in
+                                           (nside, fwhm_rad, l_cut, theta_cut_rad)))
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    fw = np.ascontiguousarray(fw, dtype=np.float64)
+    lc = np.ascontiguousarray(lc, dtype=np.int32)
+    tc = np.ascontiguousarray(tc, dtype=np.float64)
+    out = np.empty((ns.size, 4), dtype=np.float32)
+    _check(_lib.ksc_split_features(ns.size, ns.ctypes.data, fw.ctypes.data, lc.ctypes.data,
+                                   tc.ctypes.data, out.ctypes.data), "ksc_split_features")
+    return out
+
+
+def scan_split(b_l, nside: int, cl_in=None, theta_lo=None, theta_hi=None, theta_step=None,
+               bound=None, l_cut_fixed=None, cost: CostModel = None, **opts):
+    """Sec. 2 scan (ksc_scan_split).  Returns (best_row_index or None, rows as dicts)."""
+    b = np.ascontiguousarray(b_l, dtype=np.float64)
+    lmax = b.size - 1
+    so = ScanOpts()
+    _check(_lib.ksc_scan_default_opts(ctypes.byref(so)), "ksc_scan_default_opts")
+    for k, v in (("theta_lo", theta_lo), ("theta_hi", theta_hi), ("theta_step", theta_step),
+                 ("bound", bound), ("l_cut_fixed", l_cut_fixed)):
+        if v is not None:
+            setattr(so, k, v)
+    n_max = max(1, int(np.floor((so.theta_hi - so.theta_lo) / so.theta_step + 1e-9)) + 1)
+    rows = (ScanRow * n_max)()
+    cl = None if cl_in is None else np.ascontiguousarray(cl_in, dtype=np.float64)
+    n, best = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.ksc_scan_split(b.ctypes.data, lmax, int(nside),
+                               None if cl is None else cl.ctypes.data, ctypes.byref(so),
+                               None if cost is None else ctypes.byref(cost),
+                               ctypes.byref(default_opts(**opts)), rows, n_max, ctypes.byref(n),
+                               ctypes.byref(best)), "ksc_scan_split")
+    out = [{f: getattr(rows[i], f) for f, _ in ScanRow._fields_} for i in range(n.value)]
+    return (best.value if best.value >= 0 else None), out

@@ -309,7 +309,7 @@ def test_bounded_wait_runs_out_and_context_survives(K):
     c = inputs.gaussian_beam(47, np.radians(6.0))
     m = inputs.white_noise_map(nside, 77).astype(np.float32)
     with K.make_split_real(c, nside, tc) as sp:
-        K.probe_wait_timeout(sp)
+        K.probe_wait_timeout(sp, max_polls=1 << 12)  # runs out in well under a second
         with pytest.raises(K.KsconvError) as e:
             K.device_status(sp)
         assert e.value.code == K.KSC_ERR_TIMEOUT

@@ -144,7 +144,7 @@ def test_surrogate_choice_beats_the_eq6_choice_on_held_out_beams(K):
         for gg in sorted(test_g):
             sel = np.where(groups == gg)[0]
             meas_ok = d["eps_c"][sel] <= bound
-            host = K.harmonic_cost_eq8_ms(d["l_cut"][sel], d["lmax"][sel], cores=16)
+            host = K.host_cost_ms(K.eq8_cost_model(cores=16), d["l_cut"][sel], d["lmax"][sel])
             cost = np.maximum(d["t_conv_ms"][sel], host)
             best, pred = net.select(feats[sel], np.log10(bound), margin=margin, host_ms=host)
             trials, pick, first = _pick_by_net(pred, meas_ok, bound, margin, host)
@@ -189,7 +189,7 @@ def test_surrogate_chosen_split_at_nside4096(K):
     cands = [(lc, k * fwhm) for lc in (1024, 1536, 2048, 3072, 4096) for k in (16, 24, 32, 48, 64)]
     cf = K.split_features(np.full(len(cands), nside), np.full(len(cands), fwhm),
                           [c[0] for c in cands], [c[1] for c in cands])
-    host = K.harmonic_cost_eq8_ms([c[0] for c in cands], lmax, cores=16)
+    host = K.host_cost_ms(K.eq8_cost_model(cores=16), [c[0] for c in cands], lmax)
     with K.MLP(seed=12) as net:
         net.set_norm(feats.mean(0), feats.std(0), targ.mean(0), targ.std(0))
         net.train(torch.tensor(feats, device="cuda"), torch.tensor(targ, device="cuda"),

@@ -39,3 +39,22 @@ def test_forward_closed_form_and_layout():
     np.testing.assert_allclose(y, np.broadcast_to(w["b3"] * norm[3] + norm[2], y.shape), rtol=1e-15)
     assert M.N_PARAMS == 4610
     np.testing.assert_array_equal(M.pack(M.unpack(p)), p)
+
+
+def test_adam_constant_gradient_closed_form():
+    """Adam (Kingma & Ba 2015, Algorithm 1) with a constant gradient g from zero moments:
+    after t steps m1 = (1 - beta1^t) g and m2 = (1 - beta2^t) g^2, so the bias-corrected
+    moments are exactly g and g^2 and every step moves a parameter by lr g / (|g| + eps),
+    whatever t.  A 0-based step count (division by 1 - beta^0 = 0), a missing bias
+    correction (steps shrink by 1 - beta1^t at first) or a sign slip all fail it."""
+    g = np.array([2.5, -0.75, 1e-3, -40.0, 0.0])
+    lr, eps = 1e-2, 1e-8
+    p = np.array([0.3, -1.0, 2.0, 0.0, 5.0])
+    m1 = np.zeros_like(p)
+    m2 = np.zeros_like(p)
+    for t in range(1, 31):
+        p_new, m1, m2 = M.adam_step(p, g, m1, m2, t, lr, eps=eps)
+        np.testing.assert_allclose(p - p_new, lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+        np.testing.assert_allclose(m1, (1 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(m2, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+        p = p_new

@@ -131,10 +131,13 @@ def test_low_l_rows_fit_exactly_and_error_models():
 
 @pytest.mark.parametrize("continuity", [0, 2])
 def test_error_decreases_with_lcut_and_theta_cut(continuity):
-    """The binary search of Sec. 2 assumes the error falls as l_cut grows; with the
-    truncated SVD this holds over the bulk of the range (not strictly near
-    l_cut ~ l_max, where the kept subspace changes).  With the continuity
-    constraint the decrease has local rises of a few per cent."""
+    """The binary search of Sec. 2 assumes the error falls as l_cut grows.  The split
+    is solved as Sec. 2 reads (SVD of the normal matrix A^T W A with the 1e-6 cut),
+    which is not the exact least-squares minimiser (forming A^T W A squares the
+    condition number), so the decrease is not strict: over l_cut 16 -> 240 at this
+    cut (40' beam, 150', l_max 383) the reading gives Eq. 6 errors falling by 2.4x
+    with a free cut and 4.5x with the C1 cut, with local rises of at most 5% and 10%.
+    The pin holds those margins: a factor 2 and 4 overall, monotone within 5% / 10%."""
     lmax = 383
     b = O.gaussian_beam(lmax, np.radians(40 / 60))
     cl = inputs.cl_grf(lmax)
@@ -143,7 +146,7 @@ def test_error_decreases_with_lcut_and_theta_cut(continuity):
             for lc in (16, 48, 96, 160, 240)]
     rise = 1.05 if continuity == 0 else 1.10
     assert all(e2 <= e1 * rise for e1, e2 in zip(errs, errs[1:]))
-    assert errs[-1] < errs[0] / 2
+    assert errs[-1] < errs[0] / (2 if continuity == 0 else 4)
 
 
 def test_scan_returns_cheapest_feasible_pair():
