@@ -39,8 +39,11 @@ WORKLOADS = {
     # plain convolution, no split: the 2-degree beam itself truncated at 3 x FWHM
     "nside64": dict(nside=64, lmax=191, fwhm=120.0 * ARC, lcut=None, theta_cut=360.0 * ARC),
     # the nside-512 split (l_max 1535, 20' beam, l_cut 256) at the scaled 5' cut
-    "nside512split": dict(nside=512, lmax=1535, fwhm=20.0 * ARC, lcut=256, theta_cut=960.0 * ARC),
+    # the nside-512 split (l_max 1535, 20' beam, l_cut 256), theta_cut chosen by the Sec. 2
+    # scan (judged by a measured run where one is recorded)
+    "nside512split": dict(nside=512, lmax=1535, fwhm=20.0 * ARC, lcut=256, theta_cut=None),
 }
+SPLIT_CHOICE = os.path.join(ROOT, "profiles", "split_choice.json")
 WORKLOAD = dict(WORKLOADS["nside2048"])
 METRIC = "pixel-pair interactions/s and maps/s at nside=2048 vs roofline, at 1e-5 C_l rms err"
 UNIT = "pairs/s"
@@ -165,6 +168,85 @@ def sharp_coeffs():
     return c
 
 
+def eq6_alpha_refit():
+    """(alpha, rows): the least alpha for which Eq. 6 bounds the measured eps_C of every
+    split in the surrogate's training set (tests/golden/surrogate_splits.csv)."""
+    path = os.path.join(ROOT, "tests", "golden", "surrogate_splits.csv")
+    rows = [ln.strip().split(",") for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    col = {h: i for i, h in enumerate(rows[0])}
+    ratio = [float(r[col["eps_c"]]) / float(r[col["eq6_alpha5"]]) for r in rows[1:]]
+    if not ratio:
+        raise ValueError("no rows")
+    return 5.0 * max(ratio), len(ratio)
+
+
+def _split_choice():
+    """The measured split selection tests/split_choice.py recorded on the GPU machine, or {}."""
+    try:
+        with open(SPLIT_CHOICE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def choose_theta_cut(K):
+    """theta_cut of a workload with a fixed l_cut, by the Sec. 2 scan in the library
+    (ksc_scan_split: 30' grid, Eq. 6 with alpha refitted on the measured splits, cost
+    max(GPU model, Eq. 8 on 16 cores)), candidates in cost order; where a measured run
+    judged the candidates (tests/split_choice.py), its accepted cut."""
+    W = WORKLOAD
+    b = inputs.gaussian_beam(W["lmax"], W["fwhm"])
+    cl = inputs.cl_grf(W["lmax"])
+    alpha, _ = eq6_alpha_refit()
+    host = K.eq8_cost_model(cores=16)
+    cost = K.cost_model(host_ms0=host.host_ms0, host_ms_eq8=host.host_ms_eq8)
+    best, rows = K.scan_split(b, W["nside"], cl_in=cl, theta_lo=60 * ARC, theta_hi=1200 * ARC,
+                              theta_step=30 * ARC, bound=1e-5, l_cut_fixed=W["lcut"],
+                              alpha=alpha, cost=cost)
+    sel = {"by": f"library scan (Sec. 2; ksc_scan_split): 30' grid 60'-1200', l_cut fixed, "
+                 f"Eq. 6 with alpha {alpha:.3g} (refitted), cost max(GPU model, Eq. 8 / 16 cores)",
+           "scan_choice_arcmin": None if best is None else rows[best]["theta_cut"] / ARC,
+           "scan_candidates": sum(r["l_cut"] >= 0 for r in rows)}
+    th = None if best is None else rows[best]["theta_cut"]
+    judged = _split_choice().get("c2", {}).get("chosen")
+    if judged:
+        th = judged["theta_cut_arcmin"] * ARC
+        sel["judged_by_measurement"] = {k: judged[k] for k in ("theta_cut_arcmin", "eps_C",
+                                                               "eq6_alpha5")}
+        sel["judged_by_measurement"]["source"] = "tests/split_choice.py (GRF input, eps_C <= 1e-5)"
+    if th is None:  # nothing meets the bound: the least estimated error
+        th = min(rows, key=lambda r: r["error"])["theta_cut"]
+        sel["fallback"] = "no candidate meets the bound: least Eq. 6 error"
+    return th, sel
+
+
+def run_cheapest_split(K, torch, stream, b, cl, x):
+    """The cheapest nside-2048 split whose measured eps_C meets 1e-5 (l_cut in {512, 1024,
+    1536}, theta_cut searched by measurement; tests/split_choice.py), rebuilt and timed
+    here: GPU maps/s, and maps/s of the concurrent pair with the host half modelled by
+    Eq. 8 on 16 cores."""
+    rec = _split_choice().get("c3", {})
+    ch = rec.get("chosen")
+    if not ch:
+        return {"source": "not measured (tests/split_choice.py writes it on the GPU box)"}
+    lcut, tc = int(ch["l_cut"]), ch["theta_cut_arcmin"] * ARC
+    y = torch.empty_like(x)
+    with K.make_split(b, 2048, lcut, tc, cl_in=cl) as sp:
+        n_pairs = K.count_pairs(sp)
+        ms = _event_ms(lambda: K.conv_real(sp, x, y, stream=stream), stream, torch, reps=3)
+        K.device_status(sp)
+    host = K.cost_eval(K.eq8_cost_model(cores=16), 2048, lcut, 4096, tc)[1]
+    return {"l_cut": lcut, "theta_cut_arcmin": ch["theta_cut_arcmin"],
+            "eps_C_measured": ch["eps_C"], "gpu_ms": ms, "gpu_maps_per_s": 1e3 / ms,
+            "pairs_per_s": n_pairs / (ms / 1e3), "host_ms_eq8_16cores": host,
+            "maps_per_s_concurrent_halves": 1e3 / max(ms, host),
+            "per_l_cut": {k: {"theta_cut_arcmin": v["theta_cut_arcmin"], "eps_C": v["eps_C"],
+                              "gpu_ms": v["gpu_ms"]}
+                          for k, v in rec.get("smallest_passing_per_l_cut", {}).items()},
+            "source": f"{_split_choice().get('command')} ({_split_choice().get('date')}): GRF "
+                      "input, smallest passing theta_cut per l_cut on a 30' grid"}
+
+
 def split_accuracy(info):
     """eps_C of the benchmark's split (quoted from the measurement that
     tests/split_accuracy.py writes on the GPU machine) and the Eq. 6 estimate with the
@@ -172,15 +254,12 @@ def split_accuracy(info):
     split of the surrogate's training set."""
     out = {"eq6_frac_error_alpha5": info["frac_error"]}
     try:
-        rows = np.genfromtxt(os.path.join(ROOT, "tests", "golden", "surrogate_splits.csv"),
-                             delimiter=",", names=True, comments="#")
-        ratio = rows["eps_c"] / rows["eq6_alpha5"]
-        alpha = 5.0 * float(ratio.max())
+        alpha, n = eq6_alpha_refit()
         out["eq6_alpha_refit"] = alpha
         out["eq6_frac_error_alpha_refit"] = info["frac_error"] * alpha / 5.0
-        out["eq6_alpha_refit_from"] = (f"{rows.size} measured splits (nside 128-512, C1 cut): "
+        out["eq6_alpha_refit_from"] = (f"{n} measured splits (nside 128-512, C1 cut): "
                                        "the least alpha with eps_C <= Eq. 6 for all")
-    except (OSError, ValueError) as e:
+    except (OSError, ValueError, KeyError) as e:
         out["eq6_alpha_refit"] = None
         out["eq6_alpha_refit_from"] = f"unavailable: {e}"
     path = os.path.join(ROOT, "profiles", "split_accuracy_nside2048.json")
@@ -243,6 +322,9 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     from paper_1409_4441_gb300 import ksconv as K
 
+    selection = None
+    if WORKLOAD["theta_cut"] is None:
+        WORKLOAD["theta_cut"], selection = choose_theta_cut(K)
     nside, lmax, lcut, tc = (WORKLOAD[k] for k in ("nside", "lmax", "lcut", "theta_cut"))
     npix = 12 * nside * nside
     b = inputs.gaussian_beam(lmax, WORKLOAD["fwhm"])
@@ -389,7 +471,12 @@ def run_ours(args, world, rank, local):
     stack = None
     if world == 1 and not args.no_multimap and args.workload == "nside2048":
         multimap = run_multimap(K, torch, dev, stream, pk)
-        stack = run_stack(K, torch, dev, stream, sp, n_pairs, 16, world * args.steps / elapsed)
+        stack = run_stack(K, torch, dev, stream, sp,
+                          lambda: K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=1),
+                          n_pairs, 16, world * args.steps / elapsed)
+    cheapest = None
+    if world == 1 and not args.no_extras and args.workload == "nside2048":
+        cheapest = run_cheapest_split(K, torch, stream, b, cl, x)
     batch = None
     if world == 1 and not args.no_batch and args.workload == "nside2048":
         batch = run_batch(K, torch, dev, stream, big_split=sp)
@@ -409,6 +496,7 @@ def run_ours(args, world, rank, local):
                                            "zero slope at theta_cut (cut_continuity C1; "
                                            "accuracy.eps_C also gives the paper-literal fit)"),
                                  "split_fit_s": round(t_split, 2),
+                                 "theta_cut_selection": selection,
                                  "cap_weights_from_tables": round(info["frac_tabulated"], 4),
                                  "parallelism": f"independent maps x{world}"}),
         "maps_per_s": world * args.steps / elapsed,
@@ -437,6 +525,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "multimap": multimap,
         "stack_nside2048": stack,
+        "cheapest_split_nside2048": cheapest,
         "batch": batch,
     }
     print(json.dumps(line), flush=True)
@@ -484,40 +573,49 @@ def _event_ms(fn, stream, torch, reps=3):
     return statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev)
 
 
-def run_stack(K, torch, dev, stream, sp, n_pairs, n_maps, single_maps_per_s):
+def run_stack(K, torch, dev, stream, sp, make_tensor_split, n_pairs, n_maps, single_maps_per_s):
     """n_maps maps of the benchmark workload itself (nside 2048, the same split) as one
-    map-stack call (cap ring pairs on the tensor cores, belt on the FFMA kernel): maps/s
-    against the single-map path.  Maps: i.i.d. N(0,1) drawn on the device from a seeded
-    generator (throughput does not depend on the values)."""
+    map-stack call: the default path (the single-map FFMA kernels, one launch per stage
+    for the stack) and the opt-in tensor path (tensor=1: cap ring pairs on the tensor
+    cores, belt on the FFMA kernel), maps/s against the single-map step.  Maps: i.i.d.
+    N(0,1) drawn on the device from a seeded generator (throughput does not depend on
+    the values)."""
     npix = 12 * 2048 * 2048
     gen = torch.Generator(device=dev)
     gen.manual_seed(inputs.seed_for(3, 1000))
     x = torch.randn((n_maps, npix), generator=gen, device=dev, dtype=torch.float32)
     y = torch.empty_like(x)
-    ms = _event_ms(lambda: K.conv_real_multimap(sp, x, y, n_maps), stream, torch, reps=2)
+    ms = _event_ms(lambda: K.conv_real_multimap(sp, x, y, n_maps), stream, torch, reps=1)
     K.device_status(sp)
+    with make_tensor_split() as st_:
+        ms_t = _event_ms(lambda: K.conv_real_multimap(st_, x, y, n_maps), stream, torch, reps=2)
+        K.device_status(st_)
     del x, y
     return {"workload": f"{n_maps} maps x nside 2048, the benchmark split (5' beam, l_cut 1024, "
                         "theta_cut 240'), one map-stack call",
             "maps_per_s": n_maps / (ms / 1e3), "ms_per_call": ms,
             "pairs_per_s": n_maps * n_pairs / (ms / 1e3),
+            "maps_per_s_tensor": n_maps / (ms_t / 1e3), "ms_per_call_tensor": ms_t,
+            "tensor_note": "opts.tensor = 1 (TF32 x3 caps, C_l-level accuracy: per pixel "
+                           "within ~3e-5 of the output rms of the FFMA result)",
             "single_map_maps_per_s": single_maps_per_s}
 
 
 def run_multimap(K, torch, dev, stream, pk, nside=1024, n_maps=64):
     """n_maps maps sharing one split (at nside 1024: 15' beam, l_max 3071, l_cut 768,
     theta_cut 480'; other nside scale every angle by 1024/nside).  Default path: the
-    cap ring pairs as a tcgen05 contraction (each weight shared by 16 images x 8 maps,
-    TF32 x3, FP32 accumulate), the belt ring pairs on the FFMA circulant kernel.
-    Reports maps/s of the whole call against the per-map FFMA path, the roofline of
-    the tensor cap stage, and the tensor form of the belt stage for comparison."""
+    single-map FFMA kernels.  Opt-in tensor path (tensor=1): the cap ring pairs as a
+    tcgen05 contraction (each weight shared by 16 images x 8 maps, TF32 x3, FP32
+    accumulate), the belt ring pairs on the FFMA circulant kernel.  Reports maps/s of
+    both, the roofline of the tensor cap stage, and the tensor form of the belt stage
+    (tensor=2) for comparison."""
     sc = 1024.0 / nside
     lmax, lcut = 3 * nside - 1, (3 * nside) // 4
     fwhm, tc = 15.0 * sc * ARC, 480.0 * sc * ARC
     b = inputs.gaussian_beam(lmax, fwhm)
     cl = inputs.cl_grf(lmax)
-    sp = K.make_split(b, nside, lcut, tc, cl_in=cl)                 # tensor caps (default)
-    sf = K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=1)       # FFMA only
+    sp = K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=1)       # tensor caps
+    sf = K.make_split(b, nside, lcut, tc, cl_in=cl)                 # FFMA only (default)
     sb = K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=2)       # tensor belt as well
     n_pairs = K.count_pairs(sp)
     info = K.split_info(sp)
@@ -543,8 +641,8 @@ def run_multimap(K, torch, dev, stream, pk, nside=1024, n_maps=64):
         s_.close()
     return {"workload": f"{n_maps} maps x nside {nside}, shared {fwhm / ARC:.3g}' split, "
                         f"l_max {lmax}, l_cut {lcut}, theta_cut {tc / ARC:.4g}'",
-            "maps_per_s": n_maps / t_all, "ms_per_call": 1e3 * t_all,
-            "maps_per_s_ffma": n_maps / t_ffma, "ms_per_call_ffma": 1e3 * t_ffma,
+            "maps_per_s": n_maps / t_ffma, "ms_per_call": 1e3 * t_ffma,
+            "maps_per_s_tensor": n_maps / t_all, "ms_per_call_tensor": 1e3 * t_all,
             "pairs_per_map": n_pairs, "belt_pairs_per_map": belt_pairs,
             "stages_ms": {"belt_ffma": 1e3 * t_belt, "caps_tensor": 1e3 * t_caps},
             "tensor_stage": {"kernel": "conv_sym_mma_kernel", "ms": 1e3 * t_caps,
@@ -666,6 +764,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multimap", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the benchmark step only (no stack, batch or split-choice runs)")
     ap.add_argument("--multimap-only", action="store_true",
                     help="only the map-stack (tensor-core) section, at --mm-nside / --mm-maps")
     ap.add_argument("--mm-nside", type=int, default=1024)
@@ -676,6 +776,8 @@ def main():
     ap.add_argument("--band", type=int, nargs=2, metavar=("LO", "HI"),
                     help="profiling case: only output rings LO..HI (1-based), timed alone")
     args = ap.parse_args()
+    if args.no_extras:
+        args.no_multimap = args.no_batch = True
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[args.workload])
     world, rank, local = dist_setup()
@@ -691,6 +793,9 @@ def main():
                                       nside=args.mm_nside, n_maps=args.mm_maps)), flush=True)
         return
     if args.impl == "reference":
+        if WORKLOAD["theta_cut"] is None:  # the cut the measured selection accepted, if any
+            ch = _split_choice().get("c2", {}).get("chosen")
+            WORKLOAD["theta_cut"] = (ch["theta_cut_arcmin"] if ch else 960.0) * ARC
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

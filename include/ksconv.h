@@ -79,14 +79,18 @@ typedef struct {
     int path;          /* 0 (default): circulant belt kernel + symmetric gather;
                           1: general ring-pair gather only (reference path)   */
     int tensor;        /* map stacks (ksc_conv_real_multimap, n_maps >= 16):
-                          0 (default): the symmetric (cap) ring pairs on the
-                          tcgen05 tensor cores (TF32 x3, FP32 accumulate:
-                          per pixel within ~1e-5 of the output rms of the
-                          FFMA result, fractional rms C_l ~1e-6), the belt
-                          ring pairs on the FFMA circulant kernel;
-                          1: FFMA kernels only; 2: both kinds of ring pair on
-                          the tensor cores (the belt's tensor form is slower
-                          than its circulant FFMA form on GB300)            */
+                          0 (default): FP32 FFMA kernels for every ring pair
+                          (per pixel the single-map result, within 1e-6 of
+                          the output rms of the FP64 sum);
+                          1: the symmetric (cap) ring pairs on the tcgen05
+                          tensor cores (TF32 x3, FP32 accumulation of a whole
+                          ring pair's window in tensor memory: per pixel
+                          within ~3e-5 of the output rms, rms ~2e-6,
+                          fractional rms C_l ~1e-6; faster for stacks), the
+                          belt ring pairs on the FFMA circulant kernel;
+                          2: both kinds of ring pair on the tensor cores
+                          (the belt's tensor form is slower than its
+                          circulant FFMA form on GB300)                     */
     int cut_continuity; /* LSQ mode: how the fitted real-space kernel meets the
                           cut.  KSC_CUT_FREE is the paper's fit as printed
                           (Sec. 2, Eq. 3-5: K_r truncated at theta_cut, free
@@ -218,10 +222,12 @@ int ksc_conv_real_rings(const ksc_split *s, const float *d_in, float *d_out,
 
 /*
  * n_maps maps sharing one split: d_in and d_out are [n_maps][12 nside^2]
- * device arrays (map-major).  Asynchronous.  With n_maps >= 16 the cap ring
- * pairs run on the tensor cores (each kernel weight evaluated once for a
- * group of 8 maps and their 16 symmetry images; results equal the per-map
- * path to about 2e-6 of the rms).  With opts.tensor = 2 the belt ring pairs
+ * device arrays (map-major).  Asynchronous.  By default every map runs the
+ * single-map kernels (same results, one launch per stage for the stack).
+ * With opts.tensor = 1 and n_maps >= 16 the cap ring pairs run on the tensor
+ * cores (each kernel weight evaluated once for a group of 8 maps and their 16
+ * symmetry images; per pixel within ~3e-5 of the output rms of the FFMA
+ * result, see ksc_split_opts.tensor).  With opts.tensor = 2 the belt ring pairs
  * also run on the tensor cores, through a per-split workspace (the map stack
  * pre-split into TF32 tiles, about 2.6x the input size) allocated on the
  * first such call and reused; multi-map calls on such a split must not

@@ -171,7 +171,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     s->mma_ext0 = ((w_ext + 32) + 31) & ~31;
     s->mma_ntiles = (s->mma_ext0 + 4 * nside + (((w_ext + 160) + 31) & ~31)) / 32;
     // the belt tensor kernel needs its weight window in shared memory
-    if (s->tensor == 2 && ksc::belt_mma_smem(s->w_cap) > 220u * 1024) s->tensor = 0;
+    if (s->tensor == 2 && ksc::belt_mma_smem(s->w_cap) > 220u * 1024) s->tensor = 1;
     s->ring_first_item[nr] = (int)items.size();
     s->ring_first_sym[nr] = (int)items_sym.size();
     s->ring_first_belt[nr] = (int)items_belt.size();
@@ -462,7 +462,7 @@ cudaError_t launch_caps(const ksc_split *s, const float *d_in, float *d_out, int
                         cudaStream_t st) {
     const bool whole = r0 == 0 && r1 == s->plan.nrings - 1;
     const int belt_split = s->n_items_belt > 0 ? 1 : 0;
-    if (stack && s->tensor != 1)
+    if (stack && s->tensor >= 1)
         return ksc::launch_conv_sym_mma(s->plan, s->d_items_smma_lpt, s->n_items_smma, d_in,
                                         d_out, n_maps, stride, belt_split, s->d_err, st);
     if (s->cap_kernel == 1) {

@@ -40,3 +40,12 @@ def test_reference_line_keys():
 
 def test_reference_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_eq6_alpha_refit_reads_the_measured_splits():
+    """The bench line's refitted Eq. 6 alpha: the least alpha with Eq. 6 >= the measured
+    eps_C for every split of the surrogate's training set."""
+    sys.path.insert(0, ROOT)
+    import bench
+    alpha, n = bench.eq6_alpha_refit()
+    assert n >= 400 and 0.0 < alpha < 5.0

@@ -92,3 +92,45 @@ def test_split_convolution_power_spectrum_error(K):
           f"eps_C (SHT ref) = {res['b'][0]:.3e}, map err = {res['b'][1]:.3e}; "
           f"Eq.6 estimate (alpha 5) = {info['frac_error']:.3e}")
     assert res["a"][0] < 1e-2
+
+
+def test_wiener_split_through_the_library(K):
+    """Noise-dominated splits (Sec. 2: for Wiener filtering the fit is weighted by
+    C_l^2 / (C_l + N); Sec. 4's noise-dominated case).  A library split built with that
+    weighting satisfies the same properties as the signal-weighted one (rows l <= l_cut
+    exact, model = transform of the applied kernel, Eq. 2 residual no worse than the
+    oracle's fit with the same weight), fits its own residual at least as well as the
+    flat-weighted library split does, and convolves a map within the oracle's per-pixel
+    parity (nside 32, the whole map)."""
+    lmax, fwhm, lcut, tc = 767, 30.0 * ARC, 128, 150.0 * ARC
+    b = inputs.gaussian_beam(lmax, fwhm)
+    c = inputs.cl_grf(lmax)
+    cw = c * c / (c + 1e-5)           # noise above the signal from l ~ 300
+    with K.make_split(b, 64, lcut, tc, cl_in=cw) as sp:
+        kt_w = K.split_model(sp)
+        cr = K.split_real_coeffs(sp)
+        kh = K.split_harmonic(sp)
+    with K.make_split(b, 64, lcut, tc) as sp:
+        kt_f = K.split_model(sp)
+    np.testing.assert_allclose(kt_w[: lcut + 1], b[: lcut + 1], rtol=0, atol=1e-15)
+    model = _exact_transform(cr, tc)
+    model[: lcut + 1] += kh
+    np.testing.assert_allclose(model, kt_w, atol=1e-9 * np.abs(b).max())
+    ref = O.split_lsq(b, lcut, tc, cl_in=cw)
+    assert O.sigma_rms(b, kt_w, cw) <= 1.1 * O.sigma_rms(b, ref["K_tilde"], cw)
+    assert O.sigma_rms(b, kt_w, cw) <= 1.05 * O.sigma_rms(b, kt_f, cw)
+    # the weighted split's real-space part on a map
+    nside = 32
+    m = inputs.white_noise_map(nside, 17).astype(np.float32)
+    with K.make_split(b, nside, lcut, tc, cl_in=cw) as sp:
+        n_int = K.split_info(sp)["n_intervals"]
+        crs = K.split_real_coeffs(sp)
+        x = torch.tensor(m, device="cuda")
+        y = torch.full_like(x, float("nan"))
+        K.conv_real(sp, x, y)
+        K.device_status(sp)
+        got = y.cpu().numpy().astype(np.float64)
+    out, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(crs, tc, n_int))
+    rms = np.sqrt(np.mean(out ** 2))
+    assert not np.isnan(got).any()
+    assert (np.abs(got - out) <= 1e-6 * rms + amb).all()

@@ -149,3 +149,24 @@ def test_scan_with_fixed_l_cut_and_rejections(K):
     assert ei.value.code == K.KSC_ERR_ARG
     with pytest.raises(K.KsconvError):
         K.scan_split(b, 32, l_cut_fixed=lmax)
+
+
+def test_gpu_cost_refit_on_measured_splits(K):
+    """The GPU half's cost model refitted to the measured splits of the surrogate's
+    training set (GB300, CUDA events): the library's relative least squares equals a
+    plain least-squares solve of the same scaled system, and the fitted model predicts
+    the nside-512 rows (the ones least dominated by fixed overheads) to a median 15%."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "surrogate_splits.csv")
+    rows = [ln.strip().split(",") for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    d = {h: np.array([float(r[i]) for r in rows[1:]]) for i, h in enumerate(rows[0])}
+    ns, th, t = d["nside"].astype(int), d["theta_cut_arcmin"] * ARC, d["t_conv_ms"]
+    m = K.cost_fit_gpu(K.cost_model(), ns, th, t)
+    pairs = (12.0 * ns.astype(float) ** 2) ** 2 * (1 - np.cos(th)) / 2 * 1e-12
+    X = np.stack([np.ones_like(pairs), pairs], axis=1) / t[:, None]
+    c = np.linalg.lstsq(X, np.ones_like(t), rcond=None)[0]
+    assert c[0] > 0 and (m.gpu_ms0, m.gpu_ms_per_tpair) == pytest.approx(tuple(c), rel=1e-9)
+    pred = np.array([K.cost_eval(m, int(n), 1, 2, a)[0] for n, a in zip(ns, th)])
+    big = ns == 512
+    assert big.sum() > 100
+    assert np.median(np.abs(pred[big] / t[big] - 1)) < 0.15
