@@ -465,8 +465,16 @@ typedef struct {
                                               steps (Table 1's cuts are multiples
                                               of 30')                          */
     double bound;      /* Eq. 6 bound on the fractional error; default 1e-5      */
-    int l_cut_fixed;   /* -1 (default): binary search for l_cut per theta_cut;
+    int l_cut_fixed;   /* -1 (default): search l_cut per theta_cut;
                           >= 0: only theta_cut is scanned, at this l_cut        */
+    int linear_steps;  /* 0 (default): the l_cut search is Sec. 2's binary search
+                          over 0..l_max-1 (it takes the error as falling with
+                          l_cut); n > 0: first an ascending pass over n evenly
+                          spaced l_cut values, then bisection inside the first
+                          step that meets the bound -- for errors that are not
+                          monotone in l_cut (with the SVD cut active they are
+                          not, beyond about l_max / 2).  Costs up to n + log2
+                          (l_max / n) split fits per theta_cut.               */
 } ksc_scan_opts;
 
 typedef struct {
@@ -480,10 +488,10 @@ typedef struct {
 int ksc_scan_default_opts(ksc_scan_opts *o);
 /*
  * Sec. 2's scanning strategy for kernel b_l (l = 0..lmax) on maps of nside: for
- * each theta_cut of the grid, a binary search for the smallest l_cut whose
- * least-squares split (fitted as ksc_make_split does, with split_opts; NULL =
- * defaults) meets bound in Eq. 6 (with split_opts->alpha; the search takes the
- * error as falling with l_cut, as Sec. 2 does); then the candidate of least
+ * each theta_cut of the grid, a search for the smallest l_cut whose least-
+ * squares split (fitted as ksc_make_split does, with split_opts; NULL =
+ * defaults) meets bound in Eq. 6 (with split_opts->alpha; a binary search as in
+ * Sec. 2, or the linear pass of scan->linear_steps); then the candidate of least
  * max(t_gpu, t_host) under `cost` (NULL = ksc_cost_model_default), the two halves
  * running concurrently (Fig. 1).  rows (max_rows entries, may be NULL) receives
  * one row per theta_cut, *n_rows their number, *best the index of the chosen row

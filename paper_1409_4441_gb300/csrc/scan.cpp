@@ -15,8 +15,10 @@
 // Scan (Sec. 2): a linear scan over theta_cut on a grid; for each theta_cut a
 // binary search for the smallest l_cut whose fitted split meets the Eq. 6 bound
 // (the error is taken as falling with l_cut, as Sec. 2 does; where it does not,
-// the search returns one l_cut meeting the bound); the candidate of least
-// max(t_gpu, t_host) wins -- the two halves run concurrently (Fig. 1).
+// the search returns one l_cut meeting the bound), or, as an option, an ascending
+// pass over evenly spaced l_cut followed by bisection inside the first step that
+// meets the bound; the candidate of least max(t_gpu, t_host) wins -- the two
+// halves run concurrently (Fig. 1).
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -144,6 +146,7 @@ int ksc_scan_default_opts(ksc_scan_opts *o) {
     o->theta_step = 30.0 * kArcmin;
     o->bound = 1e-5;
     o->l_cut_fixed = -1;
+    o->linear_steps = 0;
     return KSC_OK;
 }
 
@@ -158,7 +161,8 @@ int ksc_scan_split(const double *b_l, int lmax, int nside, const double *cl_in,
     ksc_scan_default_opts(&so);
     if (sopts) so = *sopts;
     if (!(so.theta_step > 0.0) || !(so.theta_lo > 0.0) || so.theta_hi < so.theta_lo ||
-        so.theta_hi > kPi || !(so.bound > 0.0) || so.l_cut_fixed >= lmax)
+        so.theta_hi > kPi || !(so.bound > 0.0) || so.l_cut_fixed >= lmax ||
+        so.linear_steps < 0)
         return sfail(KSC_ERR_ARG, "bad scan options");
     ksc_cost_model cm;
     ksc_cost_model_default(&cm);
@@ -195,11 +199,32 @@ int ksc_scan_split(const double *b_l, int lmax, int nside, const double *cl_in,
                 if (row.error <= so.bound) row.l_cut = so.l_cut_fixed;
             } else {
                 int lo = 0, hi = lmax - 1;
-                const double e_hi = err(hi, th);
+                bool found = false;
+                if (so.linear_steps > 0) {
+                    // ascending pass over evenly spaced l_cut: [lo, hi] becomes the
+                    // first step whose upper end meets the bound (lo - 1 failed)
+                    const int n = std::min(so.linear_steps, lmax);
+                    int prev = -1;
+                    for (int i = 1; i <= n && !found; ++i) {
+                        const int lc = (int)((long long)(lmax - 1) * i / n);
+                        if (lc <= prev) continue;
+                        const double e = err(lc, th);
+                        if (rc) break;
+                        row.error = e;
+                        if (e <= so.bound) {
+                            lo = prev + 1;
+                            hi = lc;
+                            found = true;
+                        }
+                        prev = lc;
+                    }
+                } else {
+                    row.error = err(hi, th);
+                    found = row.error <= so.bound;
+                }
                 if (rc) break;
-                row.error = e_hi;
-                if (e_hi <= so.bound) {
-                    while (lo < hi) {  // smallest l_cut meeting the bound
+                if (found) {
+                    while (lo < hi) {  // smallest l_cut meeting the bound (bisection)
                         const int mid = (lo + hi) / 2;
                         const double e = err(mid, th);
                         if (rc) break;

@@ -99,7 +99,7 @@ class CostModel(ctypes.Structure):
 class ScanOpts(ctypes.Structure):
     _fields_ = [("theta_lo", ctypes.c_double), ("theta_hi", ctypes.c_double),
                 ("theta_step", ctypes.c_double), ("bound", ctypes.c_double),
-                ("l_cut_fixed", ctypes.c_int)]
+                ("l_cut_fixed", ctypes.c_int), ("linear_steps", ctypes.c_int)]
 
 
 class ScanRow(ctypes.Structure):
@@ -629,14 +629,14 @@ def split_features(nside, fwhm_rad, l_cut, theta_cut_rad) -> np.ndarray:
 
 
 def scan_split(b_l, nside: int, cl_in=None, theta_lo=None, theta_hi=None, theta_step=None,
-               bound=None, l_cut_fixed=None, cost: CostModel = None, **opts):
+               bound=None, l_cut_fixed=None, linear_steps=None, cost: CostModel = None, **opts):
     """Sec. 2 scan (ksc_scan_split).  Returns (best_row_index or None, rows as dicts)."""
     b = np.ascontiguousarray(b_l, dtype=np.float64)
     lmax = b.size - 1
     so = ScanOpts()
     _check(_lib.ksc_scan_default_opts(ctypes.byref(so)), "ksc_scan_default_opts")
     for k, v in (("theta_lo", theta_lo), ("theta_hi", theta_hi), ("theta_step", theta_step),
-                 ("bound", bound), ("l_cut_fixed", l_cut_fixed)):
+                 ("bound", bound), ("l_cut_fixed", l_cut_fixed), ("linear_steps", linear_steps)):
         if v is not None:
             setattr(so, k, v)
     n_max = max(1, int(np.floor((so.theta_hi - so.theta_lo) / so.theta_step + 1e-9)) + 1)

@@ -99,9 +99,12 @@ def test_wiener_split_through_the_library(K):
     C_l^2 / (C_l + N); Sec. 4's noise-dominated case).  A library split built with that
     weighting satisfies the same properties as the signal-weighted one (rows l <= l_cut
     exact, model = transform of the applied kernel, Eq. 2 residual no worse than the
-    oracle's fit with the same weight), fits its own residual at least as well as the
-    flat-weighted library split does, and convolves a map within the oracle's per-pixel
-    parity (nside 32, the whole map)."""
+    oracle's fit with the same weight) and convolves a map within the oracle's per-pixel
+    parity (nside 32, the whole map).  Each weighting fits its own residual best only
+    where the SVD cut does not bite: at the paper's 1e-6 cut the Wiener weights push one
+    more singular direction below it (139 of 148 kept against 140 for flat weights, in
+    the oracle as in the library), so the comparison of the two fits under the Wiener
+    weight is made at a 1e-10 cut."""
     lmax, fwhm, lcut, tc = 767, 30.0 * ARC, 128, 150.0 * ARC
     b = inputs.gaussian_beam(lmax, fwhm)
     c = inputs.cl_grf(lmax)
@@ -110,15 +113,17 @@ def test_wiener_split_through_the_library(K):
         kt_w = K.split_model(sp)
         cr = K.split_real_coeffs(sp)
         kh = K.split_harmonic(sp)
-    with K.make_split(b, 64, lcut, tc) as sp:
-        kt_f = K.split_model(sp)
+    with K.make_split(b, 64, lcut, tc, cl_in=cw, svd_rcond=1e-10) as sp:
+        kt_w10 = K.split_model(sp)
+    with K.make_split(b, 64, lcut, tc, svd_rcond=1e-10) as sp:
+        kt_f10 = K.split_model(sp)
     np.testing.assert_allclose(kt_w[: lcut + 1], b[: lcut + 1], rtol=0, atol=1e-15)
     model = _exact_transform(cr, tc)
     model[: lcut + 1] += kh
     np.testing.assert_allclose(model, kt_w, atol=1e-9 * np.abs(b).max())
     ref = O.split_lsq(b, lcut, tc, cl_in=cw)
     assert O.sigma_rms(b, kt_w, cw) <= 1.1 * O.sigma_rms(b, ref["K_tilde"], cw)
-    assert O.sigma_rms(b, kt_w, cw) <= 1.05 * O.sigma_rms(b, kt_f, cw)
+    assert O.sigma_rms(b, kt_w10, cw) <= 1.05 * O.sigma_rms(b, kt_f10, cw)
     # the weighted split's real-space part on a map
     nside = 32
     m = inputs.white_noise_map(nside, 17).astype(np.float32)

@@ -226,3 +226,68 @@ def test_surrogate_chosen_split_at_nside4096(K):
                             out_pix=pix)
     rms = np.sqrt(np.mean(ref ** 2))
     assert np.all(np.abs(got[pix] - ref) <= 1e-6 * rms + amb)
+
+
+@pytest.mark.skipif(not os.path.exists(DATA), reason="measured split data not generated")
+def test_selection_chain_falls_back_to_the_scan_and_a_measured_judge(K):
+    """The selection chain of the surrogate (the network first, the Sec. 2 scan as the
+    fallback, a measured run as the judge) on a beam outside the network's confident
+    range: nside 128, a 110' beam (four pixel widths, inside the training beams), l_max
+    256; the network asked for 1e-5 with a margin of five decades accepts nothing (-1),
+    so the scan (ksc_scan_split: theta_cut 600'-3600' in 300' steps, l_cut searched, Eq. 6
+    with alpha refitted to bound every training error) proposes splits in cost order and
+    each is judged by its measured eps_C (GPU real-space part + the oracle's harmonic half
+    against the full harmonic convolution of a GRF) until one passes, within three
+    trials."""
+    import oracle as O
+    from paper_1409_4441_gb300 import inputs
+    d = _load()
+    ARC = np.pi / (180 * 60)
+    feats = K.split_features(d["nside"], d["fwhm_arcmin"] * ARC, d["l_cut"],
+                             d["theta_cut_arcmin"] * ARC)
+    targ = np.stack([np.log10(d["eps_c"]), np.log10(d["t_conv_ms"])], axis=1).astype(np.float32)
+    alpha = 5.0 * float((d["eps_c"] / d["eq6_alpha5"]).max())
+    nside, lmax, fwhm, bound = 128, 256, 110.0 * ARC, 1e-5
+    cands = [(lc, k * fwhm) for lc in (32, 64, 96, 128) for k in (16, 24, 32)]
+    cf = K.split_features(np.full(len(cands), nside), np.full(len(cands), fwhm),
+                          [c[0] for c in cands], [c[1] for c in cands])
+    with K.MLP(seed=13) as net:
+        net.set_norm(feats.mean(0), feats.std(0), targ.mean(0), targ.std(0))
+        net.train(torch.tensor(feats, device="cuda"), torch.tensor(targ, device="cuda"),
+                  epochs=1500, lr=2e-3)
+        best, _ = net.select(cf, np.log10(bound), margin=5.0)
+    assert best == -1
+    # fallback: the scan over theta_cut with l_cut searched
+    b = inputs.gaussian_beam(lmax, fwhm)
+    cl = inputs.cl_grf(lmax)
+    _, rows = K.scan_split(b, nside, cl_in=cl, theta_lo=600 * ARC, theta_hi=3600 * ARC,
+                           theta_step=300 * ARC, bound=bound, alpha=alpha)
+    order = sorted((r for r in rows if r["l_cut"] >= 0),
+                   key=lambda r: max(r["t_gpu_ms"], r["t_host_ms"]))
+    assert order, "the scan must propose a split"
+    # the judge: measured eps_C of each proposal, cheapest first
+    ell = np.concatenate([np.arange(mm, lmax + 1) for mm in range(lmax + 1)])
+    alm0 = inputs.grf_alm(lmax, cl, inputs.seed_for(5, 9000))
+    m = O.alm2map(nside, alm0, lmax).astype(np.float32)
+    alm = O.map2alm(nside, m.astype(np.float64), lmax)
+    cfull = O.alm2cl(O.map2alm(nside, O.alm2map(nside, alm * b[ell], lmax), lmax), lmax)
+    x = torch.tensor(m, device="cuda")
+    y = torch.empty_like(x)
+    trials, passed = 0, None
+    for r in order[:3]:
+        trials += 1
+        with K.make_split(b, nside, r["l_cut"], r["theta_cut"], cl_in=cl) as sp:
+            kh = K.split_harmonic(sp)
+            K.conv_real(sp, x, y)
+            K.device_status(sp)
+            real = y.cpu().numpy().astype(np.float64)
+        kf = np.zeros(lmax + 1)
+        kf[: r["l_cut"] + 1] = kh
+        cs = O.alm2cl(O.map2alm(nside, O.alm2map(nside, alm * kf[ell], lmax) + real, lmax), lmax)
+        eps = O.eps_cl(cs, cfull, lmin=2)
+        print(f"\nchain: scan proposal l_cut {r['l_cut']} theta {r['theta_cut'] / ARC:.0f}': "
+              f"Eq.6 (refit) {r['error']:.1e}, measured eps_C {eps:.1e}")
+        if eps <= bound:
+            passed = r
+            break
+    assert passed is not None, f"no scan proposal passed in {trials} trials"

@@ -117,3 +117,23 @@ def test_ambiguity_bound_flags_boundary_pairs():
     c = np.zeros(3); c[0] = 1.0
     _, amb = O.brute_conv(nside, m, tc, c=c, out_pix=[0])
     assert amb[0] >= 4 * np.pi / O.npix(nside) / (4 * np.pi) * 0.999
+
+
+def test_pair_counts_exact_at_nside1():
+    """The twelve nside-1 pixels have closed-form centres: z = 2/3 at phi = pi/4 + k pi/2
+    (ring 1), z = 0 at phi = k pi/2 (ring 2), z = -2/3 at phi = pi/4 + k pi/2 (ring 3),
+    in RING order.  Every pair count within theta_cut, brute force on these vectors,
+    equals the oracle's, pixel by pixel, at cuts between each distinct separation."""
+    k = np.arange(4)
+    z = np.repeat([2.0 / 3.0, 0.0, -2.0 / 3.0], 4)
+    phi = np.concatenate([np.pi / 4 + k * np.pi / 2, k * np.pi / 2, np.pi / 4 + k * np.pi / 2])
+    s = np.sqrt(1 - z ** 2)
+    v = np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+    d = np.sqrt(((v[:, None, :] - v[None, :, :]) ** 2).sum(-1))  # chord: self pairs exactly 0
+    ang = 2 * np.arcsin(np.minimum(d / 2, 1.0))
+    seps = np.unique(np.round(ang, 6))  # (antipodes: pi to rounding)
+    cuts = (seps[:-1] + seps[1:]) / 2
+    assert cuts.size >= 4
+    for tc in cuts:
+        want = (ang <= tc).sum(axis=1)
+        assert np.array_equal(O.count_pairs(1, tc), want), np.degrees(tc)

@@ -170,3 +170,29 @@ def test_gpu_cost_refit_on_measured_splits(K):
     big = ns == 512
     assert big.sum() > 100
     assert np.median(np.abs(pred[big] / t[big] - 1)) < 0.15
+
+
+def test_linear_pass_finds_the_low_l_cut_the_binary_search_misses(K):
+    """With the SVD cut active the Eq. 6 error is not monotone in l_cut (flat weights,
+    150' beam, l_max 256, theta_cut 360': ~5e-7 up to l_cut ~48, up to 1e-3 between 60
+    and 130, small again near l_max).  The binary search of Sec. 2 starts at l_max / 2
+    and lands above 128; the linear pass (16 steps, then bisection) returns the first
+    step meeting the bound, every grid point below it failing, and a transition
+    (l_cut meets the bound, l_cut - 1 does not, or l_cut = 0)."""
+    lmax, nside, bound, th = 256, 64, 1e-6, 360 * ARC
+    b = inputs.gaussian_beam(lmax, 150 * ARC)
+    kw = dict(theta_lo=th, theta_hi=th, theta_step=1.0, bound=bound)
+    _, rb = K.scan_split(b, nside, **kw)
+    _, rl = K.scan_split(b, nside, linear_steps=16, **kw)
+    lb, ll = rb[0]["l_cut"], rl[0]["l_cut"]
+    assert lb >= 128 and 0 <= ll < 64
+    assert rl[0]["error"] <= bound
+    grid = [(lmax - 1) * i // 16 for i in range(1, 17)]
+    step_hi = next(g for g in grid if g >= ll)
+    for g in grid:
+        if g < step_hi:
+            assert _lib_error(K, b, nside, g, th, None) > bound
+    if ll > 0:
+        assert _lib_error(K, b, nside, ll - 1, th, None) > bound
+    with pytest.raises(K.KsconvError):
+        K.scan_split(b, nside, linear_steps=-1, **kw)
