@@ -52,7 +52,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, full launch);
 # absent until the current kernel has been captured
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {"conv_sym_kernel": 185942784 + 63415808}
 
 
 def workload_desc(extra=None):
@@ -240,6 +240,11 @@ def run_cheapest_split(K, torch, stream, b, cl, x):
             "eps_C_measured": ch["eps_C"], "gpu_ms": ms, "gpu_maps_per_s": 1e3 / ms,
             "pairs_per_s": n_pairs / (ms / 1e3), "host_ms_eq8_16cores": host,
             "maps_per_s_concurrent_halves": 1e3 / max(ms, host),
+            "fastest_gpu_half": min(({"l_cut": int(k), "theta_cut_arcmin": v["theta_cut_arcmin"],
+                                      "eps_C": v["eps_C"], "gpu_ms": v["gpu_ms"],
+                                      "gpu_maps_per_s": 1e3 / v["gpu_ms"]}
+                                     for k, v in rec.get("smallest_passing_per_l_cut", {}).items()),
+                                    key=lambda r: r["gpu_ms"], default=None),
             "per_l_cut": {k: {"theta_cut_arcmin": v["theta_cut_arcmin"], "eps_C": v["eps_C"],
                               "gpu_ms": v["gpu_ms"]}
                           for k, v in rec.get("smallest_passing_per_l_cut", {}).items()},
