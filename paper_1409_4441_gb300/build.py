@@ -75,7 +75,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             and all(os.path.getmtime(LIB) >= os.path.getmtime(o) for o in objs)):
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-ldl"]
     out = subprocess.run(cmd, capture_output=True, text=True)
     if out.returncode != 0:
         raise RuntimeError(f"link failed:\n{out.stdout}\n{out.stderr}")

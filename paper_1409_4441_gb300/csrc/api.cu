@@ -483,6 +483,7 @@ cudaError_t launch_caps(const ksc_split *s, const float *d_in, float *d_out, int
 // path 1: the general gather alone.
 int launch_conv(const ksc_split *s, const float *d_in, float *d_out, int n_maps,
                 long long stride, int r0, int r1, cudaStream_t st) {
+    ksc::NvtxRange range(n_maps > 1 ? "ksc_conv_real_multimap" : "ksc_conv_real");
     cudaError_t e;
     if (s->path == 1) {
         const int c = s->ring_first_item[r0], d = s->ring_first_item[r1 + 1];
@@ -589,6 +590,7 @@ int ksc_default_opts(ksc_split_opts *opts) {
 
 int ksc_make_split(const double *b_l, int lmax, int nside, int l_cut, double theta_cut,
                    const double *cl_in, const ksc_split_opts *opts, ksc_split **out) {
+    ksc::NvtxRange range("ksc_make_split");
     if (!out) return fail(KSC_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (!b_l) return fail(KSC_ERR_ARG, "null kernel");
@@ -640,6 +642,7 @@ int ksc_make_split(const double *b_l, int lmax, int nside, int l_cut, double the
 
 int ksc_make_split_real(const double *c_l, int lmax, int nside, double theta_cut,
                         const ksc_split_opts *opts, ksc_split **out) {
+    ksc::NvtxRange range("ksc_make_split_real");
     if (!out) return fail(KSC_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (!c_l) return fail(KSC_ERR_ARG, "null coefficients");
@@ -756,6 +759,7 @@ int ksc_conv_real_batch(const ksc_split *const *splits, const float *const *d_in
 }
 
 int ksc_conv_real_host(const ksc_split *cs, const float *h_in, float *h_out) {
+    ksc::NvtxRange range("ksc_conv_real_host");
     if (!cs || !h_in || !h_out) return fail(KSC_ERR_ARG, "null argument");
     ksc_split *s = const_cast<ksc_split *>(cs);
     // the split's host-path stream and buffers serve one call at a time

@@ -397,6 +397,7 @@ int ksc_batch_create(const ksc_split *const *splits, int n, const ksc_batch_opts
 }
 
 int ksc_batch_run(ksc_batch *b, const float *const *d_in, float *const *d_out, void *stream) {
+    ksc::NvtxRange range("ksc_batch_run");
     if (!b || !d_in || !d_out) return bfail(KSC_ERR_ARG, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
     int rc = set_entries(b, d_in, d_out, st);

@@ -4,12 +4,22 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <nvtx3/nvToolsExt.h>
 #include <string>
 #include <vector>
 
 #include "ksconv.h"
 
 namespace ksc {
+
+// NVTX range over a host-side scope (the enqueue of an asynchronous call, a split's
+// construction): visible to a profiler's timeline, a no-op without one.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // HEALPix RING geometry (Gorski et al. 2005), rings r = 0 .. 4n-2 (ring number
