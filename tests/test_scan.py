@@ -1,5 +1,7 @@
 """Split planning on the host (Sec. 2; no device work): the library's cost models, the
 surrogate's features and the Sec. 2 scan, against the oracle's scan and closed forms."""
+import os
+
 import numpy as np
 import pytest
 
@@ -156,7 +158,6 @@ def test_gpu_cost_refit_on_measured_splits(K):
     training set (GB300, CUDA events): the library's relative least squares equals a
     plain least-squares solve of the same scaled system, and the fitted model predicts
     the nside-512 rows (the ones least dominated by fixed overheads) to a median 15%."""
-    import os
     path = os.path.join(os.path.dirname(__file__), "golden", "surrogate_splits.csv")
     rows = [ln.strip().split(",") for ln in open(path) if ln.strip() and not ln.startswith("#")]
     d = {h: np.array([float(r[i]) for r in rows[1:]]) for i, h in enumerate(rows[0])}
@@ -196,3 +197,30 @@ def test_linear_pass_finds_the_low_l_cut_the_binary_search_misses(K):
         assert _lib_error(K, b, nside, ll - 1, th, None) > bound
     with pytest.raises(K.KsconvError):
         K.scan_split(b, nside, linear_steps=-1, **kw)
+
+
+HOST_SHT = os.path.join(os.path.dirname(__file__), "golden", "host_sht_times.csv")
+
+
+@pytest.mark.skipif(not os.path.exists(HOST_SHT),
+                    reason="host SHT times not measured")
+def test_host_cost_refit_on_timed_host_sht(K):
+    """The host half's cost model (Eq. 8's form, h0 + h1 l_cut^2 l_max / 4096^3) refitted to
+    the harmonic half timed on the GPU machine's host (tests/host_sht_costs.py): the library's
+    relative least squares equals a plain least-squares solve of the same scaled system, the
+    slope is positive, and the refit predicts the rows where the Legendre sums dominate
+    (l_cut >= 512) to a median 35%."""
+    rows = [ln.strip().split(",") for ln in open(HOST_SHT) if ln.strip() and not ln.startswith("#")]
+    d = {h: np.array([float(r[i]) for r in rows[1:]]) for i, h in enumerate(rows[0])}
+    lc, lm, t = d["l_cut"].astype(int), d["lmax"].astype(int), d["t_ms"]
+    m = K.cost_fit_host(K.cost_model(), lc, lm, t)
+    x = lc.astype(float) ** 2 * lm / 4096.0 ** 3
+    X = np.stack([np.ones_like(x), x], axis=1) / t[:, None]
+    c = np.linalg.lstsq(X, np.ones_like(t), rcond=None)[0]
+    if c[0] >= 0:
+        assert (m.host_ms0, m.host_ms_eq8) == pytest.approx(tuple(c), rel=1e-9)
+    assert m.host_ms_eq8 > 0
+    pred = np.array([K.cost_eval(m, 1, int(a), int(b), 0.1)[1] for a, b in zip(lc, lm)])
+    big = lc >= 512
+    assert big.sum() >= 2
+    assert np.median(np.abs(pred[big] / t[big] - 1)) < 0.35
