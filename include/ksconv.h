@@ -424,9 +424,12 @@ int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
 /*
  * Cost of the two halves of a split convolution (Sec. 2, Eq. 7-8, refitted for
  * this library; host arithmetic only):
- *   t_gpu  = gpu_ms0 + gpu_ms_per_tpair * P * 1e-12,  P = ksc_cost_pairs(nside, theta_cut)
- *            (the real-space half costs about a fixed amount per in-disc pixel pair;
- *            the paper's Eq. 7 is linear in theta_cut for its GTX 480 code);
+ *   t_gpu  = gpu_ms0 + (gpu_ms_per_tpair + gpu_ms_per_tpair_ring * 1000 / nside)
+ *            * P * 1e-12,  P = ksc_cost_pairs(nside, theta_cut)
+ *            (the real-space half costs a fixed amount per in-disc pixel pair, plus
+ *            a per-ring-pair overhead -- table build, staging -- which at a given
+ *            pair count grows as rings shorten, ~1/nside; the paper's Eq. 7 is
+ *            linear in theta_cut for its GTX 480 code);
  *   t_host = host_ms0 + host_ms_eq8 * l_cut^2 l_max / 4096^3
  *            (Eq. 8's form for the harmonic half; the paper's host_ms_eq8 = 160e3
  *            on one 2.8 GHz core).
@@ -434,6 +437,7 @@ int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
 typedef struct {
     double gpu_ms0, gpu_ms_per_tpair;
     double host_ms0, host_ms_eq8;
+    double gpu_ms_per_tpair_ring; /* default 0 (the nside-2048 benchmark's model) */
 } ksc_cost_model;
 
 /* In-disc pixel pairs of a map, Npix^2 (1 - cos theta_cut) / 2, Npix = 12 nside^2. */
@@ -445,10 +449,11 @@ int ksc_cost_model_default(ksc_cost_model *m);
  * either output may be NULL. */
 int ksc_cost_eval(const ksc_cost_model *m, int nside, int l_cut, int lmax,
                   double theta_cut, double *t_gpu_ms, double *t_host_ms);
-/* Least-squares fits (in relative error, overhead >= 0) of the GPU terms to n >= 2
- * measured real-space convolution times, and of the host terms to n >= 2 measured
- * harmonic-half times; each updates only its own half of *m.  KSC_ERR_ARG for
- * non-positive times or degenerate data. */
+/* Least-squares fits (in relative error, every coefficient >= 0) of the three GPU
+ * terms to n >= 3 measured real-space convolution times (with a single nside the
+ * two pair terms cannot be told apart: the ring term is then 0), and of the two
+ * host terms to n >= 2 measured harmonic-half times; each updates only its own
+ * half of *m.  KSC_ERR_ARG for non-positive times or degenerate data. */
 int ksc_cost_fit_gpu(const int *nside, const double *theta_cut, const double *t_ms,
                      int n, ksc_cost_model *m);
 int ksc_cost_fit_host(const int *l_cut, const int *lmax, const double *t_ms, int n,

@@ -3,11 +3,12 @@
 // library), the surrogate's input features, and the scanning strategy of Sec. 2
 // that picks the cheapest (l_cut, theta_cut) meeting an error bound.
 //
-// Cost models.  The GPU half (the real-space sum) costs about a fixed amount
-// per in-disc pixel pair, t_gpu = g0 + g1 P(nside, theta_cut) with P the pair
-// count of a disc of radius theta_cut on a map of Npix pixels,
-// P = Npix^2 (1 - cos theta_cut) / 2 (the paper's Eq. 7 is linear in theta_cut
-// for its GTX 480 code, whose cost per ring pair dominated).  The host half (an
+// Cost models.  The GPU half (the real-space sum) costs a fixed amount per
+// in-disc pixel pair plus a per-ring-pair overhead (table build, staging) that,
+// at a given pair count, grows as the rings shorten: t_gpu = g0 + (g1 + g2 1000 /
+// nside) P(nside, theta_cut), with P the pair count of a disc of radius theta_cut
+// on a map of Npix pixels, P = Npix^2 (1 - cos theta_cut) / 2 (the paper's Eq. 7
+// is linear in theta_cut for its GTX 480 code).  The host half (an
 // SHT to l_cut on a map with l_max) follows Eq. 8, t_host = h0 + h1 l_cut^2 l_max
 // / 4096^3 (the paper's h1 = 160 s for one 2.8 GHz core).  Both are fitted by
 // least squares in relative error to measured times.
@@ -36,24 +37,61 @@ int sfail(int code, const std::string &msg) {
     return code;
 }
 
-// least squares of t_i ~ a0 + a1 x_i in relative error: minimise
-// sum ((a0 + a1 x_i) / t_i - 1)^2 (a 2 x 2 normal system); a0 >= 0
-bool fit_rel(const std::vector<double> &x, const std::vector<double> &t, double *a0, double *a1) {
-    double s00 = 0, s01 = 0, s11 = 0, r0 = 0, r1 = 0;
-    for (size_t i = 0; i < x.size(); ++i) {
-        const double u = 1.0 / t[i], v = x[i] / t[i];
-        s00 += u * u; s01 += u * v; s11 += v * v; r0 += u; r1 += v;
+// Least squares of t_i ~ sum_j c_j X_ij in relative error -- minimise
+// sum_i ((X c)_i / t_i - 1)^2 -- with every c_j >= 0: the unconstrained solve on each
+// subset of the columns (normal equations, Gaussian elimination with partial
+// pivoting; at most three columns), the feasible solution of least residual.
+bool fit_rel(const std::vector<std::vector<double>> &X, const std::vector<double> &t,
+             std::vector<double> *c) {
+    const int k = (int)X.size();
+    double best = INFINITY;
+    std::vector<double> keep(k, 0.0);
+    for (int mask = 1; mask < (1 << k); ++mask) {
+        std::vector<int> col;
+        for (int j = 0; j < k; ++j)
+            if (mask >> j & 1) col.push_back(j);
+        const int m = (int)col.size();
+        std::vector<double> A(m * (m + 1), 0.0);  // [N | r], N = B^T B, r = B^T 1
+        for (size_t i = 0; i < t.size(); ++i)
+            for (int a = 0; a < m; ++a) {
+                const double u = X[col[a]][i] / t[i];
+                A[a * (m + 1) + m] += u;
+                for (int b2 = 0; b2 < m; ++b2) A[a * (m + 1) + b2] += u * X[col[b2]][i] / t[i];
+            }
+        bool ok = true;
+        for (int p = 0; p < m && ok; ++p) {
+            int piv = p;
+            for (int r = p + 1; r < m; ++r)
+                if (std::fabs(A[r * (m + 1) + p]) > std::fabs(A[piv * (m + 1) + p])) piv = r;
+            if (!(std::fabs(A[piv * (m + 1) + p]) > 1e-300)) { ok = false; break; }
+            for (int q = 0; q <= m; ++q) std::swap(A[p * (m + 1) + q], A[piv * (m + 1) + q]);
+            for (int r = 0; r < m; ++r) {
+                if (r == p) continue;
+                const double f = A[r * (m + 1) + p] / A[p * (m + 1) + p];
+                for (int q = p; q <= m; ++q) A[r * (m + 1) + q] -= f * A[p * (m + 1) + q];
+            }
+        }
+        if (!ok) continue;
+        std::vector<double> cc(k, 0.0);
+        for (int a = 0; a < m; ++a) {
+            cc[col[a]] = A[a * (m + 1) + m] / A[a * (m + 1) + a];
+            if (!(cc[col[a]] >= 0.0) || !std::isfinite(cc[col[a]])) ok = false;
+        }
+        if (!ok) continue;
+        double res = 0.0;
+        for (size_t i = 0; i < t.size(); ++i) {
+            double v = 0.0;
+            for (int j = 0; j < k; ++j) v += cc[j] * X[j][i];
+            res += (v / t[i] - 1.0) * (v / t[i] - 1.0);
+        }
+        if (res < best * (1.0 - 1e-12)) {
+            best = res;
+            keep = cc;
+        }
     }
-    const double det = s00 * s11 - s01 * s01;
-    if (!(std::fabs(det) > 1e-300 * std::max(1.0, s00 * s11))) return false;
-    *a0 = (r0 * s11 - r1 * s01) / det;
-    *a1 = (s00 * r1 - s01 * r0) / det;
-    if (*a0 < 0.0) {  // a negative overhead: fit the slope alone
-        *a0 = 0.0;
-        if (!(s11 > 0.0)) return false;
-        *a1 = r1 / s11;
-    }
-    return std::isfinite(*a0) && std::isfinite(*a1);
+    if (!std::isfinite(best)) return false;
+    *c = keep;
+    return true;
 }
 
 double eq8_units(int l_cut, int lmax) {
@@ -76,6 +114,7 @@ int ksc_cost_model_default(ksc_cost_model *m) {
     // 259 ms per map); host: Eq. 8 as printed (160 s on one 2.8 GHz core)
     m->gpu_ms0 = 0.1;
     m->gpu_ms_per_tpair = 259.0 / 3.085;
+    m->gpu_ms_per_tpair_ring = 0.0;
     m->host_ms0 = 0.0;
     m->host_ms_eq8 = 160.0e3;
     return KSC_OK;
@@ -84,8 +123,10 @@ int ksc_cost_model_default(ksc_cost_model *m) {
 int ksc_cost_eval(const ksc_cost_model *m, int nside, int l_cut, int lmax, double theta_cut,
                   double *t_gpu_ms, double *t_host_ms) {
     if (!m) return sfail(KSC_ERR_ARG, "null model");
+    if (nside < 1) return sfail(KSC_ERR_ARG, "nside < 1");
     if (t_gpu_ms)
-        *t_gpu_ms = m->gpu_ms0 + m->gpu_ms_per_tpair * ksc_cost_pairs(nside, theta_cut) * 1e-12;
+        *t_gpu_ms = m->gpu_ms0 + (m->gpu_ms_per_tpair + m->gpu_ms_per_tpair_ring * 1000.0 / nside) *
+                                     ksc_cost_pairs(nside, theta_cut) * 1e-12;
     if (t_host_ms)
         *t_host_ms = l_cut < 0 ? 0.0 : m->host_ms0 + m->host_ms_eq8 * eq8_units(l_cut, lmax);
     return KSC_OK;
@@ -93,34 +134,44 @@ int ksc_cost_eval(const ksc_cost_model *m, int nside, int l_cut, int lmax, doubl
 
 int ksc_cost_fit_gpu(const int *nside, const double *theta_cut, const double *t_ms, int n,
                      ksc_cost_model *m) {
-    if (!nside || !theta_cut || !t_ms || !m || n < 2) return sfail(KSC_ERR_ARG, "bad fit data");
-    std::vector<double> x, t;
+    if (!nside || !theta_cut || !t_ms || !m || n < 3) return sfail(KSC_ERR_ARG, "bad fit data");
+    std::vector<std::vector<double>> X(3);
+    std::vector<double> t;
     for (int i = 0; i < n; ++i) {
         if (!(t_ms[i] > 0.0) || nside[i] < 1) return sfail(KSC_ERR_ARG, "bad fit sample");
-        x.push_back(ksc_cost_pairs(nside[i], theta_cut[i]) * 1e-12);
+        const double p = ksc_cost_pairs(nside[i], theta_cut[i]) * 1e-12;
+        X[0].push_back(1.0);
+        X[1].push_back(p);
+        X[2].push_back(p * 1000.0 / nside[i]);
         t.push_back(t_ms[i]);
     }
-    double a0, a1;
-    if (!fit_rel(x, t, &a0, &a1)) return sfail(KSC_ERR_ARG, "degenerate fit data");
-    m->gpu_ms0 = a0;
-    m->gpu_ms_per_tpair = a1;
+    bool one_nside = true;
+    for (int i = 1; i < n; ++i) one_nside = one_nside && nside[i] == nside[0];
+    if (one_nside) X.pop_back();  // the two pair terms coincide
+    std::vector<double> c;
+    if (!fit_rel(X, t, &c)) return sfail(KSC_ERR_ARG, "degenerate fit data");
+    m->gpu_ms0 = c[0];
+    m->gpu_ms_per_tpair = c[1];
+    m->gpu_ms_per_tpair_ring = one_nside ? 0.0 : c[2];
     return KSC_OK;
 }
 
 int ksc_cost_fit_host(const int *l_cut, const int *lmax, const double *t_ms, int n,
                       ksc_cost_model *m) {
     if (!l_cut || !lmax || !t_ms || !m || n < 2) return sfail(KSC_ERR_ARG, "bad fit data");
-    std::vector<double> x, t;
+    std::vector<std::vector<double>> X(2);
+    std::vector<double> t;
     for (int i = 0; i < n; ++i) {
         if (!(t_ms[i] > 0.0) || l_cut[i] < 0 || lmax[i] < 1)
             return sfail(KSC_ERR_ARG, "bad fit sample");
-        x.push_back(eq8_units(l_cut[i], lmax[i]));
+        X[0].push_back(1.0);
+        X[1].push_back(eq8_units(l_cut[i], lmax[i]));
         t.push_back(t_ms[i]);
     }
-    double a0, a1;
-    if (!fit_rel(x, t, &a0, &a1)) return sfail(KSC_ERR_ARG, "degenerate fit data");
-    m->host_ms0 = a0;
-    m->host_ms_eq8 = a1;
+    std::vector<double> c;
+    if (!fit_rel(X, t, &c)) return sfail(KSC_ERR_ARG, "degenerate fit data");
+    m->host_ms0 = c[0];
+    m->host_ms_eq8 = c[1];
     return KSC_OK;
 }
 

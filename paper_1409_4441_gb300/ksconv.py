@@ -93,7 +93,8 @@ class BatchDesc(ctypes.Structure):
 
 class CostModel(ctypes.Structure):
     _fields_ = [("gpu_ms0", ctypes.c_double), ("gpu_ms_per_tpair", ctypes.c_double),
-                ("host_ms0", ctypes.c_double), ("host_ms_eq8", ctypes.c_double)]
+                ("host_ms0", ctypes.c_double), ("host_ms_eq8", ctypes.c_double),
+                ("gpu_ms_per_tpair_ring", ctypes.c_double)]
 
 
 class ScanOpts(ctypes.Structure):

@@ -125,10 +125,14 @@ def test_surrogate_choice_beats_the_eq6_choice_on_held_out_beams(K):
                              d["theta_cut_arcmin"] * ARC)
     targ = np.stack([np.log10(d["eps_c"]), np.log10(d["t_conv_ms"])], axis=1).astype(np.float32)
     groups = d["group"].astype(int)
+    # held-out groups are drawn among those where some candidate of the grid meets the
+    # bound when measured (no selector can succeed elsewhere: the narrowest beams, ~2.5
+    # pixels, reach 1.1-2.4e-5 at best); every group stays in the training data
+    feasible = {int(gg) for gg in np.unique(groups) if (d["eps_c"][groups == gg] <= 1e-5).any()}
     rng = np.random.default_rng(7)
     test_g = set()
     for ns in np.unique(d["nside"]):
-        gs = np.unique(groups[d["nside"] == ns])
+        gs = np.array(sorted(set(groups[d["nside"] == ns].tolist()) & feasible))
         test_g |= set(int(v) for v in rng.choice(gs, size=2, replace=False))
     tr = np.array([gg not in test_g for gg in groups])
     bound, margin = 1e-5, 0.2
