@@ -252,6 +252,34 @@ def run_cheapest_split(K, torch, stream, b, cl, x):
                       "input, smallest passing theta_cut per l_cut on a 30' grid"}
 
 
+def run_whole_split(K, torch, stream, b, cl, x):
+    """Both halves of the split convolution on the GPU (ksc_conv_real, then
+    ksc_conv_harmonic adding the harmonic half: analysis to l_cut, Khat_l, synthesis) for
+    the benchmark split and for the fastest split whose measured eps_C meets 1e-5
+    (tests/split_choice.py): maps/s of the whole convolution on one GB300, against the
+    paper's ~12 s per map on a GTX 480 + one CPU core (Sec. 3)."""
+    out = {}
+    cases = [("benchmark_split", 1024, 240.0)]
+    fast = [v for v in _split_choice().get("c3", {}).get("smallest_passing_per_l_cut", {}).values()]
+    if fast:
+        f = min(fast, key=lambda r: r["gpu_ms"])
+        cases.append(("fastest_measured_split", int(f["l_cut"]), f["theta_cut_arcmin"]))
+    y = torch.empty_like(x)
+    for name, lcut, tca in cases:
+        with K.make_split(b, 2048, lcut, tca * ARC, cl_in=cl) as sp:
+            def whole():
+                K.conv_real(sp, x, y, stream=stream)
+                K.conv_harmonic(sp, x, y, add=True, stream=stream)
+            ms = _event_ms(whole, stream, torch, reps=3)
+            ms_h = _event_ms(lambda: K.conv_harmonic(sp, x, y, add=True, stream=stream),
+                             stream, torch, reps=3)
+            K.device_status(sp)
+        out[name] = {"l_cut": lcut, "theta_cut_arcmin": tca, "ms_per_map": ms,
+                     "maps_per_s": 1e3 / ms, "harmonic_half_ms": ms_h,
+                     "real_half_ms": ms - ms_h}
+    return out
+
+
 def split_accuracy(info):
     """eps_C of the benchmark's split (quoted from the measurement that
     tests/split_accuracy.py writes on the GPU machine) and the Eq. 6 estimate with the
@@ -479,9 +507,10 @@ def run_ours(args, world, rank, local):
         stack = run_stack(K, torch, dev, stream, sp,
                           lambda: K.make_split(b, nside, lcut, tc, cl_in=cl, tensor=1),
                           n_pairs, 16, world * args.steps / elapsed)
-    cheapest = None
+    cheapest = whole_split = None
     if world == 1 and not args.no_extras and args.workload == "nside2048":
         cheapest = run_cheapest_split(K, torch, stream, b, cl, x)
+        whole_split = run_whole_split(K, torch, stream, b, cl, x)
     batch = None
     if world == 1 and not args.no_batch and args.workload == "nside2048":
         batch = run_batch(K, torch, dev, stream, big_split=sp)
@@ -531,6 +560,7 @@ def run_ours(args, world, rank, local):
         "multimap": multimap,
         "stack_nside2048": stack,
         "cheapest_split_nside2048": cheapest,
+        "whole_split_on_gpu_nside2048": whole_split,
         "batch": batch,
     }
     print(json.dumps(line), flush=True)

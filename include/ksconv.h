@@ -420,6 +420,35 @@ int ksc_probe_wait_timeout(const ksc_split *s, int max_polls, void *stream);
 int ksc_build_table_noalloc(const double *d_c, int lmax, double theta_cut,
                             int n_intervals, float *d_table, void *stream);
 
+/* ---- the harmonic half on the GPU (optional; Fig. 1's CPU half) ------- */
+/*
+ * Spherical-harmonic transforms of HEALPix RING maps up to l_max = lmax (the
+ * split's l_cut for the harmonic half), m <= lmax, real fields:
+ *   synthesis  m_p = sum_l [a_l0 Y_l0(p) + 2 Re sum_{m>0} a_lm Y_lm(p)],
+ *   analysis   a_lm = (4 pi / Npix) sum_p m_p conj(Y_lm(p))  (equal-weight
+ *              quadrature, the paper's pixel-sum convention),
+ * with Y_lm = lambda_lm(cos theta) e^{i m phi}, lambda_lm normalised associated
+ * Legendre functions without the Condon-Shortley phase.  a_lm are complex
+ * doubles (re, im interleaved) in m-major order: index(l, m) = m (2 lmax + 1 - m)
+ * / 2 + l, m = 0..lmax, l = m..lmax; (lmax + 1)(lmax + 2) / 2 entries.
+ * Legendre recurrences in FP64 (scaled against underflow near the poles), ring
+ * sums in FP32.  Device pointers; asynchronous on `stream`; scratch from the
+ * stream-ordered allocator.  nside a power of two <= 8192, 0 <= lmax <= 4 nside.
+ * Errors: KSC_ERR_ARG, KSC_ERR_NOMEM, KSC_ERR_CUDA.
+ */
+int ksc_sht_alm2map(int nside, int lmax, const double *d_alm, float *d_map,
+                    void *stream);
+int ksc_sht_map2alm(int nside, int lmax, const float *d_map, double *d_alm,
+                    void *stream);
+/*
+ * The harmonic half of the split: d_out = synthesis(Khat_l a_lm) with a_lm the
+ * analysis of d_in to l_cut (Fig. 1's CPU half, here on the GPU); add != 0
+ * adds it to d_out instead (e.g. onto ksc_conv_real's result: the whole split
+ * convolution).  KSC_ERR_ARG for a split without a harmonic part.
+ */
+int ksc_conv_harmonic(const ksc_split *s, const float *d_in, float *d_out, int add,
+                      void *stream);
+
 /* ---- split planning: cost models and the scan of Sec. 2 ---------------- */
 /*
  * Cost of the two halves of a split convolution (Sec. 2, Eq. 7-8, refitted for

@@ -240,6 +240,14 @@ void set_last_error(const std::string &msg);
 // each split construction or host-path call fail as if the device were out of
 // memory (N >= 1).  Returns true when allocation number `n` (1-based) must fail.
 bool inject_alloc_fault(int n);
+// GPU spherical-harmonic transforms (sht.cu): synthesis (add != 0 adds to the
+// map) and analysis (each a_lm scaled by d_kl[l] when d_kl is given); alm are
+// complex doubles in m-major order, sht_n_alm(lmax) of them.
+cudaError_t sht_synthesis(int nside, int lmax, const double2 *d_alm, float *d_map, int add,
+                          cudaStream_t st);
+cudaError_t sht_analysis(int nside, int lmax, const float *d_map, const double *d_kl,
+                         double2 *d_alm, cudaStream_t st);
+long long sht_n_alm(int lmax);
 
 // Largest table (intervals) a convolution kernel keeps in shared memory.
 constexpr int kMaxIntervals = 8192;

@@ -48,6 +48,7 @@ EXPORTS = [
     "ksc_mlp_n_params", "ksc_mlp_create", "ksc_mlp_set_norm", "ksc_mlp_get_params",
     "ksc_mlp_set_params", "ksc_mlp_predict", "ksc_mlp_grad", "ksc_mlp_train", "ksc_mlp_select",
     "ksc_mlp_free",
+    "ksc_sht_alm2map", "ksc_sht_map2alm", "ksc_conv_harmonic",
     "ksc_cost_pairs", "ksc_cost_model_default", "ksc_cost_eval", "ksc_cost_fit_gpu",
     "ksc_cost_fit_host", "ksc_split_features", "ksc_scan_default_opts", "ksc_scan_split",
     "ksc_status_string", "ksc_last_error",
@@ -149,6 +150,9 @@ _sig = {
     "ksc_mlp_train": [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp],
     "ksc_mlp_select": [_vp, _vp, _i, _d, _d, _vp, ctypes.POINTER(_i), _vp],
     "ksc_mlp_free": [_vp],
+    "ksc_sht_alm2map": [_i, _i, _vp, _vp, _vp],
+    "ksc_sht_map2alm": [_i, _i, _vp, _vp, _vp],
+    "ksc_conv_harmonic": [_vp, _vp, _vp, _i, _vp],
     "ksc_cost_model_default": [ctypes.POINTER(CostModel)],
     "ksc_cost_eval": [ctypes.POINTER(CostModel), _i, _i, _i, _d, _vp, _vp],
     "ksc_cost_fit_gpu": [_vp, _vp, _vp, _i, ctypes.POINTER(CostModel)],
@@ -560,6 +564,45 @@ class MLP:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _dptr_alm(t, lmax: int):
+    """Device address of a contiguous complex128 CUDA tensor of n_alm(lmax) entries."""
+    if isinstance(t, int):
+        return t
+    import torch
+    if not t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
+        raise ValueError("expected a contiguous complex128 CUDA tensor")
+    if t.numel() != n_alm(lmax):
+        raise ValueError(f"expected {n_alm(lmax)} a_lm, got {t.numel()}")
+    return t.data_ptr()
+
+
+def n_alm(lmax: int) -> int:
+    """Number of a_lm (m-major, m <= l <= lmax) of a real field."""
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def sht_alm2map(nside: int, lmax: int, d_alm, d_map, stream=None):
+    """Synthesis on the GPU (ksc_sht_alm2map): d_alm complex128 device tensor of n_alm(lmax)
+    entries (m-major), d_map float32 device tensor of 12 nside^2 pixels."""
+    _check(_lib.ksc_sht_alm2map(int(nside), int(lmax), _dptr_alm(d_alm, lmax), _dptr(d_map),
+                                _stream(stream)), "ksc_sht_alm2map")
+    return d_map
+
+
+def sht_map2alm(nside: int, lmax: int, d_map, d_alm, stream=None):
+    """Analysis on the GPU (ksc_sht_map2alm), a_lm = (4 pi / Npix) sum_p m_p Y*_lm(p)."""
+    _check(_lib.ksc_sht_map2alm(int(nside), int(lmax), _dptr(d_map), _dptr_alm(d_alm, lmax),
+                                _stream(stream)), "ksc_sht_map2alm")
+    return d_alm
+
+
+def conv_harmonic(s: Split, d_in, d_out, add: bool = False, stream=None):
+    """The split's harmonic half on the GPU (ksc_conv_harmonic); add=True adds it to d_out."""
+    _check(_lib.ksc_conv_harmonic(s.handle, _dptr(d_in), _dptr(d_out), 1 if add else 0,
+                                  _stream(stream)), "ksc_conv_harmonic")
+    return d_out
 
 
 def cost_model(**fields) -> CostModel:

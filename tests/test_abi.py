@@ -62,3 +62,12 @@ def test_null_pointers_rejected(K):
     assert lib.ksc_split_info(None, None) == K.KSC_ERR_ARG
     assert lib.ksc_make_split(None, 10, 4, 2, 0.1, None, None, None) == K.KSC_ERR_ARG
     lib.ksc_free_split(None)  # no-op
+
+
+def test_sht_arguments_rejected_before_device_work(K):
+    lib = K._lib
+    for nside, lmax in ((3, 8), (16, 65), (16, -1), (16384, 8)):
+        assert lib.ksc_sht_map2alm(nside, lmax, 16, 16, None) == K.KSC_ERR_ARG
+        assert lib.ksc_sht_alm2map(nside, lmax, 16, 16, None) == K.KSC_ERR_ARG
+    assert lib.ksc_sht_map2alm(16, 32, None, 16, None) == K.KSC_ERR_ARG
+    assert lib.ksc_conv_harmonic(None, 16, 16, 0, None) == K.KSC_ERR_ARG
