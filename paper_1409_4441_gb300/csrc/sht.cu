@@ -157,12 +157,20 @@ sht_leg_synth(int nside, int lmax, const double2 *__restrict__ alm, float2 *__re
     if (rs != r) G[(long long)rs * stride + m] = make_float2((float)(er - orr), (float)(ei - oi));
 }
 
-// e^{i pi J / L} for the exact integer J = a b mod 2L (a, b >= 0).
+// e^{i pi J / L} for the exact integer J = a b mod 2L (a, b >= 0), to about one
+// FP32 ulp: J / L = hi + lo with hi the rounded quotient and lo = (J - hi L) / L
+// (the remainder exact by the fused multiply-add), J folded into [-L, L); the
+// rounding of hi is undone to first order, e^{i pi lo} = 1 + i pi lo.
 __device__ inline float2 twiddle(long long a, long long b, int L) {
-    const long long J = (a % (2LL * L)) * (b % (2LL * L)) % (2LL * L);
+    long long J = (a % (2LL * L)) * (b % (2LL * L)) % (2LL * L);
+    if (J >= L) J -= 2LL * L;
+    const float fj = (float)J, fl = (float)L;  // exact: |J|, L <= 2^15
+    const float hi = fj / fl;
+    const float lo = fmaf(-hi, fl, fj) / fl;
     float sn, cs;
-    sincospif((float)J / (float)L, &sn, &cs);
-    return make_float2(cs, sn);
+    sincospif(hi, &sn, &cs);
+    const float d = 3.14159265f * lo;
+    return make_float2(fmaf(-sn, d, cs), fmaf(cs, d, sn));
 }
 
 __device__ inline float2 cmul(float2 a, float2 b) {
