@@ -375,6 +375,19 @@ int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw,
                           int lq, double scale, double *out);
 
 /*
+ * Host-only view (no device work) of the odd-step weight table the lockstep
+ * symmetric gather builds for one ring pair, from the same inputs as
+ * ksc_dphi_table_params plus the cells a CTA holds (cap, zero cell included).
+ * The table tabulates the ring pair's weight in the exact pixel-pair integer
+ * |N| in cubic cells of 2 lq / m integers, m odd, at the rational position
+ * P = (|N| m + off) / (2 lq): cells 0 .. nct-1 cover |N| <= ncut (the cut),
+ * cell nct is zero.  out[0] = cell width in x = dphi / 2 (radians), out[1] = m,
+ * out[2] = off, out[3] = nct (0: no table), out[4] = ncut.  Errors: KSC_ERR_ARG.
+ */
+int ksc_dphi_odd_params(double A2, double B2, double c, int n_int, double hw, int lq,
+                        double scale, int cap, double *out);
+
+/*
  * Synchronize `stream` and report device-side errors raised by earlier calls
  * on this split: KSC_ERR_TIMEOUT when a bounded wait inside a kernel ran out
  * (the kernel stopped early and its output is incomplete),

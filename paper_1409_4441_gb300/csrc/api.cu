@@ -68,6 +68,7 @@ void release(ksc_split *s) {
     cudaFree(s->d_range);
     cudaFree(s->d_pairs);
     cudaFree(s->d_xinfo);
+    cudaFree(s->d_xodd);
     cudaFree(s->d_pair_base);
     cudaFree(s->d_items);
     cudaFree(s->d_items_sym);
@@ -199,6 +200,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     for (int r = 0; r < nr; ++r) pair_base[r + 1] = pair_base[r] + (range[r].y - range[r].x + 1);
     std::vector<ksc::PairInfo> pairs((size_t)pair_base[nr]);
     std::vector<ksc::XInfo> xinfo((size_t)pair_base[nr]);
+    std::vector<ksc::XOdd> xodd((size_t)pair_base[nr]);
     {
         const double dc = s->chord_cut;
         const double cos_cut = 1.0 - 0.5 * dc * dc;
@@ -237,6 +239,13 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                                           kPi / (2.0 * (double)g.len[r] * (double)Lq),
                                           (double)n_int * (double)n_int, pi.hw, g.len[r], Lq,
                                           xscale);
+                xodd[(size_t)pair_base[r] + (q - range[r].x)] =
+                    (s->theta_cut >= kPi || o.exact_weights)
+                        ? ksc::XOdd{}
+                        : ksc::make_xodd(A * scale2, 4.0 * ss * scale2,
+                                         kPi / (2.0 * (double)g.len[r] * (double)Lq),
+                                         (double)n_int * (double)n_int, pi.hw, g.len[r], Lq,
+                                         xscale, ksc::kXCap);
             }
         }
     }
@@ -272,7 +281,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
                 if (s->path == 0 && belt_r && belt_q && !items_belt.empty()) continue;
                 const double n = cls * std::min(2.0 * pairs[ip].hw + 3.0, (double)g.len[q]);
                 all += n;
-                if (xinfo[ip].ncell > 0) tab += n;
+                if (xodd[ip].nct > 0) tab += n;
             }
         }
         s->frac_tabulated = all > 0.0 ? tab / all : 0.0;
@@ -320,6 +329,8 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
         return cuda_fail(e, "upload ring-pair table");
     if ((e = dev_upload(&s->d_xinfo, xinfo.data(), xinfo.size())) != cudaSuccess)
         return cuda_fail(e, "upload ring-pair x tables");
+    if ((e = dev_upload(&s->d_xodd, xodd.data(), xodd.size())) != cudaSuccess)
+        return cuda_fail(e, "upload ring-pair odd-step tables");
     if ((e = dev_upload(&s->d_pair_base, pair_base.data(), pair_base.size())) != cudaSuccess)
         return cuda_fail(e, "upload ring-pair offsets");
     if ((e = dev_upload(&s->d_rings, rings.data(), rings.size())) != cudaSuccess)
@@ -373,6 +384,7 @@ int finish_split(ksc_split *s, const ksc_split_opts &o) {
     p.d_range = s->d_range;
     p.d_pairs = s->d_pairs;
     p.d_xinfo = s->d_xinfo;
+    p.d_xodd = s->d_xodd;
     p.d_pair_base = s->d_pair_base;
     p.d_tab = s->d_tab;
     p.n_int = n_int;
@@ -569,6 +581,53 @@ XInfo make_xinfo(double A2, double B2, double c, double nint2, float hw, int L, 
     x.ncell = cells(shift);
     return x;
 }
+
+XOdd make_xodd(double A2, double B2, double c, double nint2, float hw, int L, int lq,
+               double scale, int cap) {
+    XOdd x{};
+    if (hw < 0.0f || 2.0f * hw + 3.0f >= (float)lq || A2 >= nint2 || B2 <= 0.0) return x;
+    const double sx2 = (nint2 - A2) / B2;  // sin^2 of x at the cut
+    if (sx2 >= 1.0) return x;
+    const double xcut = std::asin(std::sqrt(sx2));
+    // largest du/dx on [0, xcut] (as for the power-of-two tables)
+    double dmax;
+    if (A2 <= 0.0) {
+        dmax = std::sqrt(B2);
+    } else {
+        double S = (-A2 + std::sqrt(A2 * A2 + A2 * B2)) / B2;
+        S = std::min(std::max(S, 0.0), sx2);
+        dmax = B2 * std::sqrt(S * (1.0 - S) / (A2 + B2 * S));
+    }
+    if (!(dmax > 0.0)) return x;
+    const double nc = std::floor(xcut / c);
+    if (nc >= 8388608.0) return x;
+    const long long ncut = (long long)nc;
+    const long long D = 2LL * lq;
+    // widest cell within kXOddRho intervals where the chord changes fastest and no
+    // wider than the in-cut range; m the least odd integer giving a cell that narrow
+    const double hmax = std::min(scale * kXOddRho / (dmax * c), (double)ncut + 1.0);
+    long long m = (long long)std::ceil((double)D / hmax - 1e-9);
+    if (m < 1) m = 1;
+    if ((m & 1) == 0) ++m;
+    auto cells = [&](long long mm) { return (ncut * mm) / D + 1; };  // the zero cell's index
+    // wider cells (smaller odd m) while the table and its zero cell would not fit
+    while (cells(m) + 1 > cap && m > 1) m -= 2;
+    if (cells(m) + 1 > cap) return x;
+    const double width = (double)D / (double)m;  // in |N|
+    if (width * c * dmax > scale * kXRhoMax * (1.0 + 1e-12)) return x;
+    // integers a quarter warp's walk reaches (see XOdd) stay exact
+    const double reach = (double)ncut + 48.0 * (double)lq + 40.0 * (double)L;
+    if (reach >= 16777216.0 || reach * (double)m + (double)D >= 2147483647.0) return x;
+    x.m = (int)m;
+    x.nct = (int)cells(m);
+    x.off = (int)((long long)x.nct * D - ncut * m - 1);
+    x.ncut = (int)ncut;
+    const DF cm = df_from_double(c / (double)m);
+    x.cmh = cm.h;
+    x.cml = cm.l;
+    x.hc = (float)(c * width);
+    return x;
+}
 } // namespace ksc
 
 extern "C" {
@@ -671,6 +730,21 @@ int ksc_dphi_table_params(double A2, double B2, double c, int n_int, double hw, 
     out[0] = x.ncell > 0 ? std::ldexp(c, x.shift) : 0.0;
     out[1] = (double)x.ncell;
     out[2] = x.ncell > 0 ? (double)x.ncut : 0.0;
+    return KSC_OK;
+}
+
+int ksc_dphi_odd_params(double A2, double B2, double c, int n_int, double hw, int lq,
+                        double scale, int cap, double *out) {
+    if (!out || !(c > 0.0) || n_int < 1 || lq < 1 || cap < 2)
+        return fail(KSC_ERR_ARG, "bad table parameters");
+    const int L = (int)std::lround(kPi / (2.0 * c * (double)lq));
+    const ksc::XOdd x = ksc::make_xodd(A2, B2, c, (double)n_int * (double)n_int, (float)hw,
+                                       std::max(L, 1), lq, scale, cap);
+    out[0] = x.nct > 0 ? c * 2.0 * (double)lq / (double)x.m : 0.0;
+    out[1] = (double)x.m;
+    out[2] = (double)x.off;
+    out[3] = (double)x.nct;
+    out[4] = x.nct > 0 ? (double)x.ncut : 0.0;
     return KSC_OK;
 }
 

@@ -17,25 +17,22 @@
 // quarter turn) and produces all their images (no mirror on the equator ring,
 // which is its own mirror image).  Per input ring the CTA stages, for the union
 // of its threads' windows, the sixteen image sequences m[image(k')] in shared
-// memory so that every image of input position k' sits at the same offset; each
-// thread then walks the union of its classes' windows four positions at a time:
-// 4 C kernel weights, then one 16-byte shared load per image feeding 4 C FFMAs.
-// The sixteen images of a position are loaded once for the C classes: shared-
-// memory bandwidth to the lanes (a 16-byte load by a warp costs four wavefronts
-// whatever its addresses) is what bounds this gather, and C classes per thread
-// divide the image traffic per pixel pair by C.
+// memory so that every image of input position k' sits at the same offset.
 //
 // A weight depends on the pixel pair only through the exact integer
 // N = (2k + t) L' - (2k' + t') L (dphi / 2 = N pi / (2 L L')).  Per input ring
-// the CTA first builds the ring pair's weight table in |N| in shared memory
-// (cubic cells of 2^shift integers whose last cell ends exactly at the cut,
-// followed by a zero cell, ksc_sym.cuh); a weight is then a table position
-// p = min(|N| + off, nct 2^shift) 2^-shift (exact), its cell floor(p) and offset
-// p - floor(p) (exact), one 16-byte cell load and three FMAs, and it is exactly
-// zero beyond the cut with no test.  Ring pairs without a table (whole-ring
-// windows, or more cells than a CTA holds) evaluate the double-float chord and
-// the K_r table per pair (ksc_device.cuh).  FP32 partial sums over 64 positions
-// are Kahan-folded into the totals.
+// the CTA builds the ring pair's odd-step weight table (XOdd: cubic cells of
+// 2 L' / m in |N|, m odd, ksc_sym.cuh) in shared memory, and the eight lanes of
+// each quarter warp walk the same input positions (the lockstep path below):
+// their table positions then differ by whole cells, m C per lane (an odd
+// number), so a quarter's eight 16-byte cell loads fall in eight different bank
+// groups, and one exact rational position per quarter serves all its weights.
+// A weight is a cell load and three FMAs, exactly zero beyond the cut with no
+// test; four positions of a thread then take one 16-byte shared load per image
+// feeding 4 C FFMAs.  Ring pairs without a table (whole-ring windows, or more
+// cells than a CTA holds) evaluate the double-float chord and the K_r table per
+// pair (ksc_device.cuh).  FP32 partial sums over 64 positions are Kahan-folded
+// into the totals.
 #include <cstdint>
 
 #include "ksc_device.cuh"
@@ -70,12 +67,12 @@ __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
 }
 
 // floor(a / b), ceil(a / b) for b > 0
-__device__ __forceinline__ int floor_div(int a, int b) {
-    const int q = a / b;
+__device__ __forceinline__ long long floor_div_ll(long long a, long long b) {
+    const long long q = a / b;
     return (a % b != 0 && a < 0) ? q - 1 : q;
 }
-__device__ __forceinline__ int ceil_div(int a, int b) {
-    const int q = a / b;
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) {
+    const long long q = a / b;
     return (a % b != 0 && a > 0) ? q + 1 : q;
 }
 
@@ -108,56 +105,293 @@ __device__ __forceinline__ void fold(float *sum, float *comp, float *part) {
     }
 }
 
-// Constants of the table path for one ring pair: table positions are
-// p = min(|N| + off, nct 2^shift) 2^-shift.
-struct TabPos {
-    float inv, offS, ncf;  // 2^-shift, off 2^-shift, nct
-    float step, dcls;      // per position (2 L) and per class (2 L') in table units
+// ---------------------------------------------------------------------------
+// Lockstep table path.  The eight lanes of a quarter warp own classes
+// kQ + C l .. kQ + C l + C - 1 (l = 0..7) and walk the same input positions, a
+// quad of four at a time, from the first in-cut position of the quarter's first
+// class to the last of its last class; the four quarters of a warp walk in step
+// (each from its own start), so every lane reads the same image float4 as the
+// other lanes of its quarter.  At position p the quarter's first class has
+// N = NQ(p) = numQ - 2 L p, and class c of lane l has N = NQ + 2 L' (C l + c).
+// The ring pair's odd-step table (XOdd) has cells of 2 L' / m in |N|, so with
+// P = (|N| m + off) / (2 L'):
+//   N >= 0:  P = PQ + m (C l + c),   PQ = (NQ m + off) / (2 L'),
+//   N <= 0:  P = PN - m (C l + c),   PN = (-NQ m + off) / (2 L'),
+// one rational position per quarter and position, shared by its 8 C weights:
+// the offset in the cell is common, the cells of the eight lanes are m C apart
+// (odd), and the quarter's eight 16-byte cell loads fall in eight different bank
+// groups.  PQ and PN are carried exactly as integer + remainder / (2 L') (the
+// remainder an integer-valued float below 2^16).  Quads where every lane has
+// N >= 0 (or <= 0) take one state; the few quads where the quarter's lanes
+// straddle N = 0 take both and choose per weight.  Positions beyond a class's cut
+// read the zero cell (indices clamped to it), so no weight needs a mask.
+// ---------------------------------------------------------------------------
+
+// Exact position state integer + remainder / D (0 <= remainder < D).
+struct OddPos {
+    int a;    // floor of the position
+    float R;  // remainder (an integer, as a float)
 };
 
-// The four weights of the quad at table position tp (class c, first position).
-__device__ __forceinline__ float4 tab_quad(const float4 *xt, const TabPos &x, float tp) {
-    float4 w;
-    w.x = xtab_at(xt, fminf(fabsf(tp) + x.offS, x.ncf));
-    w.y = xtab_at(xt, fminf(fabsf(tp - x.step) + x.offS, x.ncf));
-    w.z = xtab_at(xt, fminf(fabsf(fmaf(-2.0f, x.step, tp)) + x.offS, x.ncf));
-    w.w = xtab_at(xt, fminf(fabsf(fmaf(-3.0f, x.step, tp)) + x.offS, x.ncf));
-    return w;
+__device__ __forceinline__ OddPos odd_pos(long long M, int D) {
+    long long a = M / D;
+    if (a * D > M) --a;  // floor
+    return OddPos{(int)a, (float)(M - a * D)};
 }
 
-// Table path.  Positions a..b of one staged segment (s0: its first position):
-// the union of the thread's classes' windows within the cut.  Every weight
-// beyond a class's cut is exactly zero (the table's zero cell), so no position
-// needs a mask.  The loop is software-pipelined: the next quad's weights are
-// looked up while the current quad's FFMAs run.
-template <class S, bool MIRROR>
-__device__ __forceinline__ void acc_table(const float4 *xt, const TabPos &x, const float *st,
-                                          int s0, int a, int b, int num, int L, float *sum,
-                                          float *comp, float *part) {
+// Step constants: one position (N down by 2 L) moves PQ down and PN up by
+// (2 L m) / D = q1 + r1 / D.
+struct OddStep {
+    int q1;
+    unsigned nct;  // the zero cell
+    float r1, Df, invD;
+};
+
+__device__ __forceinline__ void pos_down(OddPos &s, const OddStep &k) {
+    s.R -= k.r1;
+    const bool b = s.R < 0.0f;
+    s.R = b ? s.R + k.Df : s.R;
+    s.a -= k.q1 + (b ? 1 : 0);
+}
+__device__ __forceinline__ void pos_up(OddPos &s, const OddStep &k) {
+    s.R += k.r1;
+    const bool b = s.R >= k.Df;
+    s.R = b ? s.R - k.Df : s.R;
+    s.a += k.q1 + (b ? 1 : 0);
+}
+
+__device__ __forceinline__ float odd_weight(const float4 *xt, int idx, unsigned nct, float f) {
+    return hermite(xt[min((unsigned)idx, nct)], f);
+}
+
+// Weights of one quad, every lane's N of one sign: SIGN > 0 walks PQ (kk[c] =
+// m (C l + c) added), SIGN < 0 walks PN (subtracted).  The state advances by the
+// quad's four positions.
+template <int C, int SIGN>
+__device__ __forceinline__ void quad_fast(const float4 *xt, OddPos &s, const OddStep &k,
+                                          const int *kk, float4 *w) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const float f = s.R * k.invD;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float v = odd_weight(xt, SIGN > 0 ? s.a + kk[c] : s.a - kk[c], k.nct, f);
+            if (d == 0) w[c].x = v;
+            else if (d == 1) w[c].y = v;
+            else if (d == 2) w[c].z = v;
+            else w[c].w = v;
+        }
+        if (SIGN > 0) pos_down(s, k);
+        else pos_up(s, k);
+    }
+}
+
+// Weights of one quad whose lanes straddle N = 0: per weight the sign of the
+// lane's N = NQ + 2 L' (C l + c) (NQ >= thr[c] = -2 L' (C l + c) means N >= 0).
+template <int C>
+__device__ __forceinline__ void quad_mixed(const float4 *xt, OddPos &sp, OddPos &sn, int &NQ,
+                                           int Dl, const OddStep &k, const int *kk,
+                                           const int *thr, float4 *w) {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const float fp = sp.R * k.invD, fn = sn.R * k.invD;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const bool pos = NQ >= thr[c];
+            const float v = odd_weight(xt, pos ? sp.a + kk[c] : sn.a - kk[c], k.nct,
+                                       pos ? fp : fn);
+            if (d == 0) w[c].x = v;
+            else if (d == 1) w[c].y = v;
+            else if (d == 2) w[c].z = v;
+            else w[c].w = v;
+        }
+        pos_down(sp, k);
+        pos_up(sn, k);
+        NQ -= Dl;
+    }
+}
+
+// Quads j in [ja, jb) of one regime for this lane's quarter (first position
+// p0 = QA4 + 4 ja, local offset in the staged segment p0 - s0).  Software-
+// pipelined: the next quad's weights are looked up while the current quad's
+// FFMAs run.
+template <class S, bool MIRROR, int SIGN>
+__device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int loc, int nquads,
+                                         OddPos s, const OddStep &k, const int *kk, float *sum,
+                                         float *comp, float *part, int &nfold) {
     constexpr int C = S::C;
-    int kq = s0 + ((a - s0) & ~3);
-    // exact: the thread's positions lie within a few of every class's window, where
-    // |N| < 2^24
-    float tp = (float)(num - 2 * L * kq) * x.inv;  // class 0 at the first quad
-    float4 wc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) wc[c] = tab_quad(xt, x, fmaf((float)c, x.dcls, tp));
-    int nq = 0;
-    for (; kq + 4 <= b; kq += 4) {
-        tp = fmaf(-4.0f, x.step, tp);
-        float4 wn[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) wn[c] = tab_quad(xt, x, fmaf((float)c, x.dcls, tp));
-        fma_quad<S, MIRROR>(st, kq - s0, wc, part);
-#pragma unroll
-        for (int c = 0; c < C; ++c) wc[c] = wn[c];
-        if (++nq == kFold) {
-            nq = 0;
+    for (int q = 0; q < nquads; ++q) {
+        float4 w[C];
+        quad_fast<C, SIGN>(xt, s, k, kk, w);
+        fma_quad<S, MIRROR>(st, loc, w, part);
+        loc += 4;
+        if (++nfold == kFold) {
+            nfold = 0;
             fold<S>(sum, comp, part);
         }
     }
-    fma_quad<S, MIRROR>(st, kq - s0, wc, part);  // the last quad (kq <= b < kq + 4)
+}
+
+template <class S, bool MIRROR>
+__device__ __forceinline__ void run_mixed(const float4 *xt, const float *st, int loc, int nquads,
+                                          OddPos sp, OddPos sn, int NQ, int Dl, const OddStep &k,
+                                          const int *kk, const int *thr, float *sum, float *comp,
+                                          float *part, int &nfold) {
+    constexpr int C = S::C;
+    for (int q = 0; q < nquads; ++q) {
+        float4 w[C];
+        quad_mixed<C>(xt, sp, sn, NQ, Dl, k, kk, thr, w);
+        fma_quad<S, MIRROR>(st, loc, w, part);
+        loc += 4;
+        if (++nfold == kFold) {
+            nfold = 0;
+            fold<S>(sum, comp, part);
+        }
+    }
+}
+
+// One ring pair through the lockstep path.  Returns false (before any work, and
+// the same in every thread) when a warp's quarters spread wider than a staged
+// segment; the caller then takes the per-pair path.
+template <class S, bool MIRROR>
+__device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &g, int c0,
+                                              int n_cls, int t, int L,
+                                              const float *__restrict__ m, float *st,
+                                              float4 *xt, int *sW, float *sum, float *comp,
+                                              float *part) {
+    constexpr int T = S::T, C = S::C, kSpan = S::kSpan, kStride = S::kStride, NW = T / 32;
+    const int tid = threadIdx.x, wid = tid >> 5, ql = tid & 7;
+    const int L2 = g.len, Q2 = L2 / 4;
+    const int D = 2 * L2, Dl = 2 * L;
+    const long long ncut = g.oncut;
+    // this lane's quarter: classes kQ .. kQ + 8 C - 1 (those below n_cls exist)
+    const int kQ = c0 + C * (tid & ~7);
+    const int kQe = min(kQ + 8 * C - 1, n_cls - 1);
+    const long long numQ = (long long)(2 * kQ + t) * L2 - (long long)g.phase * L;
+    const long long numQL = numQ + 2LL * L2 * (8 * C - 1);
+    const long long numQe = numQ + 2LL * L2 * (kQe - kQ);
+    // in-cut positions of the quarter's existing classes: |num - 2 L p| <= ncut
+    const long long QA = ceil_div_ll(numQ - ncut, Dl), QB = floor_div_ll(numQe + ncut, Dl);
+    const int QA4 = (int)(QA & ~3LL);
+    const int Jq = (kQ < n_cls && QB >= QA) ? (int)((QB - QA4) >> 2) + 1 : 0;
+    const int Jw = __reduce_max_sync(0xffffffffu, Jq);
+    const int loW = __reduce_min_sync(0xffffffffu, Jq > 0 ? QA4 : 0x7fffffff);
+    const int hiW = __reduce_max_sync(0xffffffffu, Jq > 0 ? QA4 : (int)0x80000000);
+    // regimes over quads j = 0 .. Jw - 1 (p = QA4 + 4 j): every lane's N >= 0 while
+    // NQ(p + 3) >= 0; every lane's N <= 0 once NQ(p) + 2 L' (8 C - 1) <= 0
+    int jPq = Jw, jNq = 0;
+    if (Jq > 0) {
+        jPq = (int)max(0LL, min((long long)Jw, floor_div_ll(numQ - (long long)Dl * (QA4 + 3),
+                                                            4LL * Dl) + 1));
+        jNq = (int)max(0LL, min((long long)Jw, ceil_div_ll(numQL - (long long)Dl * QA4,
+                                                           4LL * Dl)));
+    }
+    const int jP = __reduce_min_sync(0xffffffffu, jPq);
+    const int jN = max(jP, __reduce_max_sync(0xffffffffu, jNq));
+
+    __syncthreads();  // the previous ring pair's table, segment and sW reads are done
+    if ((tid & 31) == 0) {
+        sW[4 * wid + 0] = Jw;
+        sW[4 * wid + 1] = loW;
+        sW[4 * wid + 2] = hiW;
+    }
+    xodd_build<T>(P, g, xt);
+    __syncthreads();
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    bool wide = false;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const int J = sW[4 * w], l = sW[4 * w + 1], h = sW[4 * w + 2];
+        if (J > 0) {
+            lo = min(lo, l);
+            hi = max(hi, h + 4 * J - 1);
+            wide = wide || (h - l + 8 > kSpan);
+        }
+    }
+    if (wide) return false;
+    if (lo > hi) return true;  // no class of this item has a pair within the cut
+
+    // per lane: table offsets and sign thresholds of its classes, step constants
+    int kk[C], thr[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        kk[c] = g.om * (C * ql + c);
+        thr[c] = -2 * L2 * (C * ql + c);
+    }
+    OddStep k;
+    {
+        const long long st1 = (long long)Dl * g.om;
+        k.q1 = (int)(st1 / D);
+        k.r1 = (float)(st1 - (long long)k.q1 * D);
+        k.Df = (float)D;
+        k.invD = 1.0f / (float)D;
+        k.nct = (unsigned)g.onct;
+    }
+    int jnext = 0;  // the warp's next quad
+    int nfold = 0;
+    for (int s0 = lo;;) {
+        const int span = min(kSpan, ((hi - s0 + 1) + 3) & ~3);
+        // stage the sixteen image sequences of positions s0 .. s0 + span - 1
+        for (int j = tid; j < span; j += T) {
+            const int kp = s0 + j;
+            const int idx = sym_pmod(kp, L2);
+            const int idr = sym_pmod(Q2 - kp - g.phase, L2);
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                int ia = idx + qq * Q2;
+                if (ia >= L2) ia -= L2;
+                int ib = idr + qq * Q2;
+                if (ib >= L2) ib -= L2;
+                st[qq * kStride + j] = __ldg(m + g.start + ia);
+                st[(8 + qq) * kStride + j] = __ldg(m + g.start + ib);
+                if constexpr (MIRROR) {
+                    st[(4 + qq) * kStride + j] = __ldg(m + g.start_m + ia);
+                    st[(12 + qq) * kStride + j] = __ldg(m + g.start_m + ib);
+                }
+            }
+        }
+        __syncthreads();
+        // quads of this warp inside the segment: every quarter's quad within it
+        int jB = jnext;
+        if (Jw > 0 && jnext < Jw)
+            jB = max(jnext, min(Jw, (int)floor_div_ll((long long)s0 + span - 4 - hiW, 4) + 1));
+        if (Jq > 0 && jB > jnext) {
+            const int loc0 = QA4 + 4 * jnext - s0;
+            // [jnext, jB) split into N >= 0, mixed and N <= 0 quads
+            const int e1 = min(jB, max(jnext, jP));
+            const int e2 = min(jB, max(e1, jN));
+            if (e1 > jnext) {
+                const long long NQ = numQ - (long long)Dl * (QA4 + 4 * jnext);
+                run_fast<S, MIRROR, 1>(xt, st, loc0, e1 - jnext, odd_pos(NQ * g.om + g.ooff, D),
+                                       k, kk, sum, comp, part, nfold);
+            }
+            if (e2 > e1) {
+                const long long NQ = numQ - (long long)Dl * (QA4 + 4 * e1);
+                run_mixed<S, MIRROR>(xt, st, loc0 + 4 * (e1 - jnext), e2 - e1,
+                                     odd_pos(NQ * g.om + g.ooff, D),
+                                     odd_pos(-NQ * g.om + g.ooff, D), (int)NQ, Dl, k, kk, thr,
+                                     sum, comp, part, nfold);
+            }
+            if (jB > e2) {
+                const long long NQ = numQ - (long long)Dl * (QA4 + 4 * e2);
+                run_fast<S, MIRROR, -1>(xt, st, loc0 + 4 * (e2 - jnext), jB - e2,
+                                        odd_pos(-NQ * g.om + g.ooff, D), k, kk, sum, comp, part,
+                                        nfold);
+            }
+        }
+        jnext = jB;
+        // the next segment starts at the first quad some warp has left
+        if ((tid & 31) == 0) sW[4 * wid + 3] = jnext < Jw ? loW + 4 * jnext : 0x7fffffff;
+        __syncthreads();
+        int nxt = 0x7fffffff;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) nxt = min(nxt, sW[4 * w + 3]);
+        if (nxt == 0x7fffffff) break;
+        __syncthreads();  // every thread has read sW and consumed the segment
+        s0 = nxt;
+    }
     fold<S>(sum, comp, part);
+    return true;
 }
 
 // Per-pair path (no table): the four kernel weights of quad kq (zero outside
@@ -213,7 +447,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                                          bool skip_belt_inputs, bool add, int band_lo,
                                          int band_hi, const float *__restrict__ m,
                                          float *__restrict__ o, SymRing *sR, float *st,
-                                         float4 *xt, int *__restrict__ err) {
+                                         float4 *xt, int *sW, int *__restrict__ err) {
     constexpr int T = S::T, C = S::C, kSpan = S::kSpan, kStride = S::kStride;
     const int tid = threadIdx.x;
     const DevRing R = P.d_rings[r];
@@ -235,6 +469,16 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             const SymRing g = sR[qi];
             if (g.hw < 0.0f) continue;
             const int L2 = g.len, Q2 = L2 / 4;
+            // invariant the arithmetic relies on (the host's split construction
+            // guarantees it): class integers fit in int32
+            if (tid == 0 &&
+                (long long)(2 * c0 + t) * L2 + 2LL * S::kClasses * L2 > 2147483647LL)
+                atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
+            // the odd-step table, when the ring pair has one that fits
+            if (g.onct > 0 && g.onct + 1 <= S::kXCap &&
+                lockstep_pair<S, MIRROR>(P, g, c0, n_cls, t, L, m, st, xt, sW, sum, comp, part))
+                continue;
+            // per-pair weights: the union of this thread's classes' windows
             long long num0, numx;
             int lo[C], hi[C], U0, U1, dummy;
 #pragma unroll
@@ -245,26 +489,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
             }
             sym_window(k_first, t, L, g, &numx, &U0, &dummy);
             sym_window(k_last, t, L, g, &numx, &dummy, &U1);
-            // table with its last cell ending at the cut (plus one zero cell)
-            const int off = (-(g.ncut + 1)) & ((1 << g.shift) - 1);
-            const int nct = (g.ncut + 1 + off) >> g.shift;
-            const bool use_xt = g.ncell > 0 && nct + 1 <= S::kXCap;
-            // the union of this thread's classes' windows (within the cut for tables)
-            int wa = lo[0], wb = hi[C - 1];
-            if (use_xt) {
-                wa = max(wa, ceil_div((int)num0 - g.ncut, 2 * L));
-                wb = min(wb, floor_div((int)(num0 + 2LL * (C - 1) * L2) + g.ncut, 2 * L));
-                __syncthreads();  // the previous ring pair's lookups are done
-                xtab_build_cut<S::T>(P, g, xt, off, nct);  // (published by the next barrier)
-            }
-            const TabPos x{g.inv, (float)off * g.inv, (float)nct, (float)(2 * L) * g.inv,
-                           (float)(2 * L2) * g.inv};
-            // invariants the arithmetic relies on (the host's split construction
-            // guarantees them): class integers fit in int32, and table positions within
-            // a few positions of the cut stay exact in FP32
-            if (tid == 0 && (num0 + 2LL * S::kClasses * L2 > 2147483647LL ||
-                             (use_xt && (long long)g.ncut + 32LL * L >= (1LL << 24))))
-                atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
+            const int wa = lo[0], wb = hi[C - 1];
             for (int s0 = U0 & ~3; s0 <= U1; s0 += kSpan) {
                 // positions this segment needs (the union ends at U1)
                 const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
@@ -293,9 +518,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 if (a > b) continue;
                 // (classes without a reflection partner accumulate the reflected
                 // images too; those sums are never written)
-                if (use_xt)
-                    acc_table<S, MIRROR>(xt, x, st, s0, a, b, (int)num0, L, sum, comp, part);
-                else if (g.small)
+                if (g.small)
                     acc_pairs<S, MIRROR, 1>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
                 else
                     acc_pairs<S, MIRROR, 0>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
@@ -341,7 +564,8 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
 template <class S>
 __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0, int belt_split,
                                              int band_lo, int band_hi, const float *m, float *o,
-                                             SymRing *sR, float *st, float4 *xt, int *err) {
+                                             SymRing *sR, float *st, float4 *xt, int *sW,
+                                             int *err) {
     const int eq = (P.nrings - 1) / 2;  // the equator ring, its own mirror image
     const DevRing R = P.d_rings[ring];
     const int Q = R.len / 4;
@@ -349,9 +573,11 @@ __device__ __forceinline__ void sym_dispatch(const ConvPlan &P, int ring, int k0
     const bool belt = ring >= P.belt_lo && ring <= P.belt_hi;
     const bool add = belt_split && belt;
     if (ring == eq)
-        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt, err);
+        sym_item<S, false>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt, sW,
+                           err);
     else
-        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt, err);
+        sym_item<S, true>(P, ring, k0, n_cls, add, add, band_lo, band_hi, m, o, sR, st, xt, sW,
+                          err);
 }
 
 // One split; grid.y runs over maps.  CTAs claim items in list order through a
@@ -365,6 +591,7 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
                 int belt_split, int band_lo, int band_hi, int *__restrict__ counters,
                 int *__restrict__ err) {
     __shared__ SymRing sR[kRingChunk];
+    __shared__ int sW[4 * (S::T / 32)];  // per-warp walk extents (lockstep path)
     __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
     extern __shared__ float4 xt[];  // S::kXCap cells
@@ -377,7 +604,7 @@ conv_sym_kernel(const ConvPlan P, const WorkItem *__restrict__ items, int n_item
         const int it = s_next;
         if (it >= n_items) break;
         const WorkItem w = items[it];
-        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st, xt, err);
+        sym_dispatch<S>(P, w.ring, w.k0, belt_split, band_lo, band_hi, m, o, sR, st, xt, sW, err);
     }
 }
 
@@ -389,6 +616,7 @@ conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__re
                       const int4 *__restrict__ items, int n_items, int *__restrict__ counter,
                       int *__restrict__ err) {
     __shared__ SymRing sR[kRingChunk];
+    __shared__ int sW[4 * (S::T / 32)];  // per-warp walk extents (lockstep path)
     __shared__ __align__(16) float st[kImg * S::kStride];
     __shared__ int s_next;
     extern __shared__ float4 xt[];  // S::kXCap cells
@@ -401,7 +629,7 @@ conv_sym_batch_kernel(const ConvPlan *__restrict__ plans, const BatchEntry *__re
         const int4 w = items[it];
         const BatchEntry e = entries[w.x];
         const ConvPlan &P = plans[e.plan];
-        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st, xt,
+        sym_dispatch<S>(P, w.y, w.z, e.belt_split, 0, P.nrings - 1, e.in, e.out, sR, st, xt, sW,
                         err);
     }
 }

@@ -78,6 +78,32 @@ __host__ __device__
 #endif
 inline int kXPad(int L, int shift) { return ((6 * L) >> shift) + 2; }
 
+// Weight table of one ring pair for the lockstep symmetric gather (conv_sym.cu).
+// The eight lanes of a quarter warp walk the same input positions for classes
+// C apart, so at one position their |N| differ by 2 lq C per lane (lq the input
+// ring's length).  Cells of width 2 lq / m in |N| with m odd put those lanes m C
+// cells apart: for odd C an odd step, so the eight 16-byte cells a quarter warp
+// reads lie in eight different shared-memory bank groups.  A pair's table
+// position is the rational P = (|N| m + off) / (2 lq): cell floor(P), offset
+// P - floor(P), computed exactly from integers.  off puts a cell boundary
+// between |N| = ncut (in the cut) and ncut + 1: cells 0 .. nct-1 hold cubics in
+// the offset, cell nct is zero, and every position beyond it is clamped to it.
+struct XOdd {
+    int m;          // odd; cell width 2 lq / m
+    int off;        // 0 <= off < 2 lq
+    int nct;        // zero cell (0: no table)
+    int ncut;       // largest |N| within the cut
+    float cmh, cml; // c / m as a double-float pair: x of one unit of 2 lq j - off
+    float hc;       // x extent of one cell, 2 lq c / m
+    int pad;
+};
+constexpr double kXOddRho = 1.5;  // chord-table intervals per cell (at most) ...
+// ... widened up to kXRhoMax while the cells would not fit (cells + 1 <= cap).
+// The walk of a quarter warp visits positions up to (8 C) lq / L + 16 beyond a
+// class's cut: the host keeps |N| there below 2^24 and |N| m + 2 lq below 2^31.
+XOdd make_xodd(double A2, double B2, double c, double nint2, float hw, int L, int lq,
+               double scale, int cap);
+
 // Host: the table parameters of ring pair (r, q); A2, B2 are the ring-pair
 // constants scaled to table-position units, c = pi / (2 L lq), L and lq the
 // output and input rings' lengths, hw the window half-width (whole-ring windows
@@ -134,6 +160,7 @@ struct ConvPlan {
     const int2 *d_range;     // per output ring: first/last input ring (0-based)
     const PairInfo *d_pairs; // ring-pair geometry, d_pair_base[r] + (q - range.x)
     const XInfo *d_xinfo;    // x tables of the symmetric gather, same indexing
+    const XOdd *d_xodd;      // odd-step tables of the lockstep gather, same indexing
     const int *d_pair_base;
     const float4 *d_tab;     // table
     int n_int;
@@ -269,6 +296,7 @@ struct ksc_split {
     int2 *d_range = nullptr;
     ksc::PairInfo *d_pairs = nullptr;
     ksc::XInfo *d_xinfo = nullptr;
+    ksc::XOdd *d_xodd = nullptr;
     double frac_tabulated = 0.0;  // share of gather weights from dphi tables
     int *d_pair_base = nullptr;
     // work lists, each with a per-ring prefix (nrings + 1 offsets)

@@ -22,6 +22,10 @@ struct SymRing {  // one (output ring, input ring) pair
     int shift, ncut, ncell;  // ncell 0: no table
     float inv;    // 2^-shift
     float pcl;    // ncut 2^-shift: the largest in-cut table position
+    // odd-step table of the lockstep gather (XOdd): cells of 2 len / om in |N|
+    int om, ooff, onct, oncut;  // onct 0: no table
+    DF ocm;       // c / om
+    float ohc;    // x extent of one cell
 };
 
 __device__ __forceinline__ int sym_pmod(int a, int n) {
@@ -53,6 +57,13 @@ __device__ __forceinline__ SymRing load_sym_ring(const ConvPlan &P, int r, int q
     g.ncell = g.hw < 0.0f ? 0 : xi.ncell;
     g.inv = __int_as_float((127 - xi.shift) << 23);  // 2^-shift
     g.pcl = (float)xi.ncut * g.inv;
+    const XOdd xo = P.d_xodd[P.d_pair_base[r] + (q - rg.x)];
+    g.om = xo.m;
+    g.ooff = xo.off;
+    g.onct = g.hw < 0.0f ? 0 : xo.nct;
+    g.oncut = xo.ncut;
+    g.ocm = DF{xo.cmh, xo.cml};
+    g.ohc = xo.hc;
     return g;
 }
 
@@ -166,6 +177,60 @@ __device__ __forceinline__ void xtab_build_cut(const ConvPlan &P, const SymRing 
     for (int j = j0; j < j1; ++j) {
         float w1, d1;
         xtab_node(P, g, j + 1, &w1, &d1, off);
+        const float dw = w1 - w0;
+        xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
+                            fmaf(-2.0f, dw, d0 + d1));
+        w0 = w1;
+        d0 = d1;
+    }
+}
+
+// Node j of a ring pair's odd-step table (XOdd): the weight at table position
+// P = j, |N| = (2 len j - off) / om (negative below the first in-range node:
+// the weight is even in N), and its slope per cell, from the same double-float
+// chord and K_r table as xtab_node.
+__device__ __forceinline__ void xodd_node(const ConvPlan &P, const SymRing &g, int j, float *w,
+                                          float *d) {
+    const int n = 2 * g.len * j - g.ooff;  // < 2^31 (host check)
+    const float nh = (float)n;
+    const float nl = (float)(n - (int)nh);  // exact remainder
+    const float xh = nh * g.ocm.h;
+    const float xl = fmaf(nh, g.ocm.h, -xh) + fmaf(nh, g.ocm.l, nl * g.ocm.h);
+    const DF s = sin_df(xh, xl);
+    const float s2h = s.h * s.h;
+    const float s2l = fmaf(2.0f * s.h, s.l, fmaf(s.h, s.h, -s2h));
+    const float ph = g.B.h * s2h;
+    const float pl = fmaf(g.B.h, s2h, -ph) + fmaf(g.B.h, s2l, g.B.l * s2h);
+    const float dh = g.A.h + ph;
+    const float bp = dh - g.A.h;
+    const float e = (g.A.h - (dh - bp)) + (ph - bp);
+    const float dl = e + g.A.l + pl;
+    const float rr = rsqrtf(fmaxf(dh, 1e-30f));
+    const float uh = dh * rr;
+    const float ul = (fmaf(-uh, uh, dh) + dl) * (0.5f * rr);
+    const int i = max(0, min((int)floorf(uh), P.n_int - 1));
+    const float f = (uh - (float)i) + ul;
+    const float4 cf = __ldg(&P.d_tab[i]);
+    *w = hermite(cf, f);
+    const float dk = fmaf(f, fmaf(f, 3.0f * cf.w, 2.0f * cf.z), cf.y);  // dK/du
+    const float dudx = g.B.h * s.h * __cosf(xh) * rr;
+    *d = dk * dudx * g.ohc;
+}
+
+// The odd-step table in shared memory, built by the T threads of a CTA: cells
+// 0 .. onct-1 from the weights and slopes at their two boundaries, cell onct zero.
+template <int T>
+__device__ __forceinline__ void xodd_build(const ConvPlan &P, const SymRing &g, float4 *xt) {
+    const int nct = g.onct;
+    const int per = ((nct + T - 1) / T) | 1;
+    const int j0 = threadIdx.x * per, j1 = min(j0 + per, nct);
+    if (threadIdx.x == 0) xt[nct] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (j0 >= j1) return;
+    float w0, d0;
+    xodd_node(P, g, j0, &w0, &d0);
+    for (int j = j0; j < j1; ++j) {
+        float w1, d1;
+        xodd_node(P, g, j + 1, &w1, &d1);
         const float dw = w1 - w0;
         xt[j] = make_float4(w0, d0, fmaf(3.0f, dw, -fmaf(2.0f, d0, d1)),
                             fmaf(-2.0f, dw, d0 + d1));

@@ -41,7 +41,8 @@ EXPORTS = [
     "ksc_split_harmonic", "ksc_split_real_coeffs", "ksc_split_model", "ksc_split_table",
     "ksc_conv_real", "ksc_conv_real_rings", "ksc_conv_real_multimap", "ksc_conv_real_batch",
     "ksc_conv_real_host", "ksc_conv_real_stage", "ksc_conv_real_multimap_stage",
-    "ksc_count_pairs", "ksc_device_status", "ksc_dphi_table_params", "ksc_probe_wait_timeout",
+    "ksc_count_pairs", "ksc_device_status", "ksc_dphi_table_params", "ksc_dphi_odd_params",
+    "ksc_probe_wait_timeout",
     "ksc_free_split", "ksc_build_table_noalloc",
     "ksc_batch_default_opts", "ksc_batch_create", "ksc_batch_run", "ksc_batch_autotune",
     "ksc_batch_info", "ksc_batch_status", "ksc_batch_free",
@@ -129,6 +130,7 @@ _sig = {
     "ksc_conv_real_multimap_stage": [_vp, _vp, _vp, _i, _i, _vp],
     "ksc_count_pairs": [_vp, ctypes.POINTER(ctypes.c_longlong)],
     "ksc_dphi_table_params": [_d, _d, _d, _i, _d, _i, _d, _vp],
+    "ksc_dphi_odd_params": [_d, _d, _d, _i, _d, _i, _d, _i, _vp],
     "ksc_probe_wait_timeout": [_vp, ctypes.c_int, _vp],
     "ksc_device_status": [_vp, _vp],
     "ksc_free_split": [_vp],
@@ -321,6 +323,17 @@ def dphi_table_params(A2: float, B2: float, c: float, n_int: int, hw: float, lq:
            "ksc_dphi_table_params")
     return {"dx": float(out[0]), "ncell": int(out[1]), "ncut": float(out[2])}
 
+
+def dphi_odd_params(A2: float, B2: float, c: float, n_int: int, hw: float, lq: int,
+                    scale: float = 1.0, cap: int = 4096) -> dict:
+    """ksc_dphi_odd_params: the lockstep gather's odd-step table of one ring pair
+    (cell width in x = dphi/2, m, off, zero cell nct, ncut); host only."""
+    out = np.zeros(5)
+    _check(_lib.ksc_dphi_odd_params(float(A2), float(B2), float(c), int(n_int), float(hw),
+                                    int(lq), float(scale), int(cap), out.ctypes.data),
+           "ksc_dphi_odd_params")
+    return {"width": out[0], "m": int(out[1]), "off": int(out[2]), "nct": int(out[3]),
+            "ncut": int(out[4])}
 
 def probe_wait_timeout(s: Split, max_polls: int = 0, stream=None):
     """Run the bounded-wait failure path once (max_polls <= 0: the kernels' limit)."""
