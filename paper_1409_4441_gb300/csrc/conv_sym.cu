@@ -67,12 +67,12 @@ __device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
 }
 
 // floor(a / b), ceil(a / b) for b > 0
-__device__ __forceinline__ long long floor_div_ll(long long a, long long b) {
-    const long long q = a / b;
+__device__ __forceinline__ int floor_div(int a, int b) {
+    const int q = a / b;
     return (a % b != 0 && a < 0) ? q - 1 : q;
 }
-__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) {
-    const long long q = a / b;
+__device__ __forceinline__ int ceil_div(int a, int b) {
+    const int q = a / b;
     return (a % b != 0 && a > 0) ? q + 1 : q;
 }
 
@@ -133,16 +133,15 @@ struct OddPos {
     float R;  // remainder (an integer, as a float)
 };
 
-__device__ __forceinline__ OddPos odd_pos(long long M, int D) {
-    long long a = M / D;
-    if (a * D > M) --a;  // floor
-    return OddPos{(int)a, (float)(M - a * D)};
+__device__ __forceinline__ OddPos odd_pos(int M, int D) {
+    const int a = floor_div(M, D);
+    return OddPos{a, (float)(M - a * D)};
 }
 
 // Step constants: one position (N down by 2 L) moves PQ down and PN up by
 // (2 L m) / D = q1 + r1 / D.
 struct OddStep {
-    int q1;
+    int q1, D2;    // D2 = 2 L' (N between consecutive classes)
     unsigned nct;  // the zero cell
     float r1, Df, invD;
 };
@@ -187,17 +186,17 @@ __device__ __forceinline__ void quad_fast(const float4 *xt, OddPos &s, const Odd
 }
 
 // Weights of one quad whose lanes straddle N = 0: per weight the sign of the
-// lane's N = NQ + 2 L' (C l + c) (NQ >= thr[c] = -2 L' (C l + c) means N >= 0).
+// lane's N = NQ + 2 L' (C l + c) (N >= 0 while NQ >= thr0 - c 2 L').
 template <int C>
 __device__ __forceinline__ void quad_mixed(const float4 *xt, OddPos &sp, OddPos &sn, int &NQ,
                                            int Dl, const OddStep &k, const int *kk,
-                                           const int *thr, float4 *w) {
+                                           int thr0, float4 *w) {
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const float fp = sp.R * k.invD, fn = sn.R * k.invD;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const bool pos = NQ >= thr[c];
+            const bool pos = NQ >= thr0 - c * k.D2;
             const float v = odd_weight(xt, pos ? sp.a + kk[c] : sn.a - kk[c], k.nct,
                                        pos ? fp : fn);
             if (d == 0) w[c].x = v;
@@ -235,12 +234,12 @@ __device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int 
 template <class S, bool MIRROR>
 __device__ __forceinline__ void run_mixed(const float4 *xt, const float *st, int loc, int nquads,
                                           OddPos sp, OddPos sn, int NQ, int Dl, const OddStep &k,
-                                          const int *kk, const int *thr, float *sum, float *comp,
+                                          const int *kk, int thr0, float *sum, float *comp,
                                           float *part, int &nfold) {
     constexpr int C = S::C;
     for (int q = 0; q < nquads; ++q) {
         float4 w[C];
-        quad_mixed<C>(xt, sp, sn, NQ, Dl, k, kk, thr, w);
+        quad_mixed<C>(xt, sp, sn, NQ, Dl, k, kk, thr0, w);
         fma_quad<S, MIRROR>(st, loc, w, part);
         loc += 4;
         if (++nfold == kFold) {
@@ -263,28 +262,29 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
     const int tid = threadIdx.x, wid = tid >> 5, ql = tid & 7;
     const int L2 = g.len, Q2 = L2 / 4;
     const int D = 2 * L2, Dl = 2 * L;
-    const long long ncut = g.oncut;
-    // this lane's quarter: classes kQ .. kQ + 8 C - 1 (those below n_cls exist)
+    const int ncut = g.oncut;
+    // this lane's quarter: classes kQ .. kQ + 8 C - 1 (those below n_cls exist); class
+    // integers fit in int32 (checked by the caller)
     const int kQ = c0 + C * (tid & ~7);
     const int kQe = min(kQ + 8 * C - 1, n_cls - 1);
-    const long long numQ = (long long)(2 * kQ + t) * L2 - (long long)g.phase * L;
-    const long long numQL = numQ + 2LL * L2 * (8 * C - 1);
-    const long long numQe = numQ + 2LL * L2 * (kQe - kQ);
+    const int numQ = (2 * kQ + t) * L2 - g.phase * L;
+    const int numQe = numQ + 2 * L2 * (kQe - kQ);
     // in-cut positions of the quarter's existing classes: |num - 2 L p| <= ncut
-    const long long QA = ceil_div_ll(numQ - ncut, Dl), QB = floor_div_ll(numQe + ncut, Dl);
-    const int QA4 = (int)(QA & ~3LL);
-    const int Jq = (kQ < n_cls && QB >= QA) ? (int)((QB - QA4) >> 2) + 1 : 0;
+    const int QA = ceil_div(numQ - ncut, Dl), QB = floor_div(numQe + ncut, Dl);
+    const int QA4 = QA & ~3;
+    const int Jq = (kQ < n_cls && QB >= QA) ? ((QB - QA4) >> 2) + 1 : 0;
     const int Jw = __reduce_max_sync(0xffffffffu, Jq);
     const int loW = __reduce_min_sync(0xffffffffu, Jq > 0 ? QA4 : 0x7fffffff);
     const int hiW = __reduce_max_sync(0xffffffffu, Jq > 0 ? QA4 : (int)0x80000000);
-    // regimes over quads j = 0 .. Jw - 1 (p = QA4 + 4 j): every lane's N >= 0 while
-    // NQ(p + 3) >= 0; every lane's N <= 0 once NQ(p) + 2 L' (8 C - 1) <= 0
+    // N of the quarter's first class at its first position (small: near the cut;
+    // the products wrap, the difference is exact)
+    const int NQ0 = (int)((unsigned)numQ - (unsigned)Dl * (unsigned)QA4);
+    // regimes over quads j (p = QA4 + 4 j): every lane's N >= 0 while NQ(p + 3) >= 0;
+    // every lane's N <= 0 once NQ(p) + 2 L' (8 C - 1) <= 0
     int jPq = Jw, jNq = 0;
     if (Jq > 0) {
-        jPq = (int)max(0LL, min((long long)Jw, floor_div_ll(numQ - (long long)Dl * (QA4 + 3),
-                                                            4LL * Dl) + 1));
-        jNq = (int)max(0LL, min((long long)Jw, ceil_div_ll(numQL - (long long)Dl * QA4,
-                                                           4LL * Dl)));
+        jPq = max(0, min(Jw, floor_div(NQ0 - 3 * Dl, 4 * Dl) + 1));
+        jNq = max(0, min(Jw, ceil_div(NQ0 + 2 * L2 * (8 * C - 1), 4 * Dl)));
     }
     const int jP = __reduce_min_sync(0xffffffffu, jPq);
     const int jN = max(jP, __reduce_max_sync(0xffffffffu, jNq));
@@ -311,24 +311,24 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
     if (wide) return false;
     if (lo > hi) return true;  // no class of this item has a pair within the cut
 
-    // per lane: table offsets and sign thresholds of its classes, step constants
-    int kk[C], thr[C];
+    // per lane: table offsets of its classes, step constants
+    int kk[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        kk[c] = g.om * (C * ql + c);
-        thr[c] = -2 * L2 * (C * ql + c);
-    }
+    for (int c = 0; c < C; ++c) kk[c] = g.om * (C * ql + c);
+    const int thr0 = -2 * L2 * C * ql;  // lane's N >= 0 while NQ >= thr0 - c 2 L'
     OddStep k;
     {
-        const long long st1 = (long long)Dl * g.om;
-        k.q1 = (int)(st1 / D);
-        k.r1 = (float)(st1 - (long long)k.q1 * D);
+        const int st1 = Dl * g.om;
+        k.q1 = st1 / D;
+        k.r1 = (float)(st1 - k.q1 * D);
         k.Df = (float)D;
+        k.D2 = D;
         k.invD = 1.0f / (float)D;
         k.nct = (unsigned)g.onct;
     }
     int jnext = 0;  // the warp's next quad
     int nfold = 0;
+    const bool single = hi - lo + 1 <= kSpan;  // one segment: no reduction between segments
     for (int s0 = lo;;) {
         const int span = min(kSpan, ((hi - s0 + 1) + 3) & ~3);
         // stage the sixteen image sequences of positions s0 .. s0 + span - 1
@@ -354,31 +354,32 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
         // quads of this warp inside the segment: every quarter's quad within it
         int jB = jnext;
         if (Jw > 0 && jnext < Jw)
-            jB = max(jnext, min(Jw, (int)floor_div_ll((long long)s0 + span - 4 - hiW, 4) + 1));
+            jB = max(jnext, min(Jw, floor_div(s0 + span - 4 - hiW, 4) + 1));
         if (Jq > 0 && jB > jnext) {
             const int loc0 = QA4 + 4 * jnext - s0;
             // [jnext, jB) split into N >= 0, mixed and N <= 0 quads
             const int e1 = min(jB, max(jnext, jP));
             const int e2 = min(jB, max(e1, jN));
             if (e1 > jnext) {
-                const long long NQ = numQ - (long long)Dl * (QA4 + 4 * jnext);
+                const int NQ = NQ0 - 4 * Dl * jnext;
                 run_fast<S, MIRROR, 1>(xt, st, loc0, e1 - jnext, odd_pos(NQ * g.om + g.ooff, D),
                                        k, kk, sum, comp, part, nfold);
             }
             if (e2 > e1) {
-                const long long NQ = numQ - (long long)Dl * (QA4 + 4 * e1);
+                const int NQ = NQ0 - 4 * Dl * e1;
                 run_mixed<S, MIRROR>(xt, st, loc0 + 4 * (e1 - jnext), e2 - e1,
                                      odd_pos(NQ * g.om + g.ooff, D),
-                                     odd_pos(-NQ * g.om + g.ooff, D), (int)NQ, Dl, k, kk, thr,
-                                     sum, comp, part, nfold);
+                                     odd_pos(-NQ * g.om + g.ooff, D), NQ, Dl, k, kk, thr0, sum,
+                                     comp, part, nfold);
             }
             if (jB > e2) {
-                const long long NQ = numQ - (long long)Dl * (QA4 + 4 * e2);
+                const int NQ = NQ0 - 4 * Dl * e2;
                 run_fast<S, MIRROR, -1>(xt, st, loc0 + 4 * (e2 - jnext), jB - e2,
                                         odd_pos(-NQ * g.om + g.ooff, D), k, kk, sum, comp, part,
                                         nfold);
             }
         }
+        if (single) break;
         jnext = jB;
         // the next segment starts at the first quad some warp has left
         if ((tid & 31) == 0) sW[4 * wid + 3] = jnext < Jw ? loW + 4 * jnext : 0x7fffffff;
