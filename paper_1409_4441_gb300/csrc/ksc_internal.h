@@ -97,7 +97,7 @@ struct XOdd {
     float hc;       // x extent of one cell, 2 lq c / m
     int pad;
 };
-constexpr double kXOddRho = 2.0;  // chord-table intervals per cell (at most) ...
+constexpr double kXOddRho = 1.5;  // chord-table intervals per cell (at most) ...
 // ... widened up to kXRhoMax while the cells would not fit (cells + 1 <= cap).
 // The walk of a quarter warp visits positions up to (8 C) lq / L + 16 beyond a
 // class's cut: the host keeps |N| there below 2^24 and |N| m + 2 lq below 2^31.

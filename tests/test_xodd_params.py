@@ -8,7 +8,7 @@ classes are C apart then sit m C cells apart, an odd number.  For ring pairs of 
 RING grid (geometry written out here from the public ring definitions, as in
 test_xtable_params.py) at the benchmark's cut and at a wide cut, the table must: use an odd
 m; place the cut exactly (|N| = ncut in the last cubic cell, ncut + 1 in the zero cell);
-fit a CTA's cells with its zero cell; keep a cell within 2 K_r-table intervals of the
+fit a CTA's cells with its zero cell; keep a cell within 1.5 K_r-table intervals of the
 chord where the chord changes fastest unless the cells would not fit (then within 3), and
 no wider than the in-cut range; and keep every integer a quarter warp's walk reaches exact.
 du/dx is sampled independently of the library's closed-form maximum.
@@ -93,23 +93,23 @@ def test_odd_cells_place_the_cut_and_fit(K, nside, theta_cut, n_int):
         assert nct == cells(ncut, m, lq)
         assert nct + 1 <= CAP
         assert t["width"] == pytest.approx(c * D / m, rel=1e-14)
-        # the steepest du/dx, sampled: a cell spans at most 2 intervals where the
+        # the steepest du/dx, sampled: a cell spans at most 1.5 intervals where the
         # cells fit, and never more than 3
         xs = np.linspace(0.0, xcut, 20001)
         u = np.sqrt(A2 + B2 * np.sin(xs) ** 2)
         dmax = np.max(B2 * np.sin(xs) * np.cos(xs) / np.maximum(u, 1e-300))
         rho = t["width"] * dmax
         assert rho <= 3.0 * (1 + 1e-3)
-        assert D / m <= ncut + 1 + 1e-9 or rho <= 2.0 * (1 + 1e-3)
-        if rho > 2.0 * (1 + 1e-3):
+        assert D / m <= ncut + 1 + 1e-9 or rho <= 1.5 * (1 + 1e-3)
+        if rho > 1.5 * (1 + 1e-3):
             # widened only because the next finer odd m would not fit
             assert cells(ncut, m + 2, lq) + 1 > CAP, (i, iq, m)
             seen["widened"] += 1
         else:
-            # the least odd m within 2 intervals (and the in-cut range)
+            # the least odd m within 1.5 intervals (and the in-cut range)
             if m > 1:
                 w2 = c * D / (m - 2)
-                assert w2 * dmax > 2.0 * (1 - 1e-3) or D / (m - 2) > ncut + 1
+                assert w2 * dmax > 1.5 * (1 - 1e-3) or D / (m - 2) > ncut + 1
             seen["table"] += 1
         # integers the walk reaches stay exact: |N| below 2^24, |N| m + 2 lq below 2^31
         reach = ncut + 48 * lq + 40 * L
