@@ -52,7 +52,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, full launch);
 # absent until the current kernel has been captured
-DRAM_TRAFFIC = {"conv_sym_kernel": 185942784 + 63415808}
+DRAM_TRAFFIC = {"conv_sym_kernel": 227899904 + 67889408}
 
 
 def workload_desc(extra=None):
@@ -542,10 +542,11 @@ def run_ours(args, world, rank, local):
                                      "dram__bytes_write.sum of one full-size launch)",
                      "note": "2 FLOP (one FMA) per in-disc pixel pair the kernel handles; "
                              "peak = 152 SMs x 128 FP32 lanes x 2 x max SM clock; the cap "
-                             "gather is bound by shared-memory bandwidth to the lanes "
-                             "(ncu l1tex__throughput, l1tex__data_bank_conflicts_pipe_lsu_"
-                             "mem_shared_op_ld: its weight-cell loads are random across "
-                             "lanes)"},
+                             "gather is bound by instruction issue at 8 warps per SM "
+                             "(ncu smsp__issue_active ~53%, about a third of the issued "
+                             "instructions useful FFMAs: per 16 FFMAs a weight costs a "
+                             "table-cell load, an index and three FMAs; stalls on fixed "
+                             "latency, staging loads and barriers)"},
         "target": {"roofline_frac": 0.5, "met": bool(achieved / peak_tflops >= 0.5),
                    "step_frac": 2.0 * n_pairs / statistics.mean(launch_ms) * 1e3 / 1e12
                    / peak_tflops},
