@@ -44,6 +44,7 @@ namespace {
 
 constexpr int kRingChunk = 32;  // ring-pair constants staged per pass
 constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, reflected}
+constexpr int kPair = 8;        // image pairs (north, south mirror): FP32x2 operands
 constexpr int kFold = 16;       // quads per FP32 partial sum (64 positions)
 // Tile shape: T threads of C classes each, SPAN staged input positions per
 // segment (each image row padded by 4 floats), MINB resident CTAs per SM the
@@ -59,11 +60,14 @@ using ShapeSmall = SymShape<128, 1, 448, 3, 2048>;  // variant 1: 128 classes, 3
 using ShapeWide = SymShape<128, 1, 448, 2, kXCap>;  // variant 2: 128 classes, full tables
 static_assert(ShapeC3::kSpan % 4 == 0 && ShapeSmall::kSpan % 4 == 0, "quad-aligned spans");
 
-__device__ __forceinline__ void kahan(float *sum, float *comp, float v) {
-    const float y = v - *comp;
-    const float tt = *sum + y;
-    *comp = (tt - *sum) - y;
-    *sum = tt;
+// Kahan step on a pair of sums (every operation rounds to nearest, as in the
+// scalar form: v - c = fma(c, -1, v) and (t - s) - y = fma(y, -1, fma(s, -1, t))).
+__device__ __forceinline__ void kahan2(float2 &sum, float2 &comp, float2 v) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 y = __ffma2_rn(comp, m1, v);
+    const float2 t = __fadd2_rn(sum, y);
+    comp = __ffma2_rn(y, m1, __ffma2_rn(sum, m1, t));
+    sum = t;
 }
 
 // floor(a / b), ceil(a / b) for b > 0
@@ -76,32 +80,64 @@ __device__ __forceinline__ int ceil_div(int a, int b) {
     return (a % b != 0 && a > 0) ? q + 1 : q;
 }
 
-// Sixteen (or, on the equator, eight) images of one quad of positions for the C
-// classes of a thread: one 16-byte shared load per image, 4 C FFMAs.
-template <class S, bool MIRROR>
-__device__ __forceinline__ void fma_quad(const float *st, int j, const float4 *w, float *part) {
+// The sixteen images of one quad of positions for the C classes of a thread.  The
+// staged images are stored as eight (north, south mirror) pairs interleaved by
+// position, so one 16-byte shared load gives two positions of a pair, and each
+// multiply-add is a paired FP32 FMA (two images, one weight): 32 paired FMAs per
+// class and quad.  (On the equator ring, its own mirror, the south halves hold
+// zeros and their sums are never written.)
+template <class S>
+__device__ __forceinline__ void fma_quad(const float *st, int j, const float4 *w, float2 *part) {
 #pragma unroll
-    for (int i = 0; i < kImg; ++i) {
-        if (!MIRROR && (i & 4)) continue;
-        const float4 v = *reinterpret_cast<const float4 *>(st + i * S::kStride + j);
+    for (int r = 0; r < kPair; ++r) {
+        const float *row = st + r * 2 * S::kStride + 2 * j;
+        const float4 a = *reinterpret_cast<const float4 *>(row);
+        const float4 b = *reinterpret_cast<const float4 *>(row + 4);
 #pragma unroll
         for (int c = 0; c < S::C; ++c) {
-            float p = part[c * kImg + i];
-            p = fmaf(w[c].x, v.x, p);
-            p = fmaf(w[c].y, v.y, p);
-            p = fmaf(w[c].z, v.z, p);
-            p = fmaf(w[c].w, v.w, p);
-            part[c * kImg + i] = p;
+            float2 p = part[c * kPair + r];
+            p = __ffma2_rn(make_float2(w[c].x, w[c].x), make_float2(a.x, a.y), p);
+            p = __ffma2_rn(make_float2(w[c].y, w[c].y), make_float2(a.z, a.w), p);
+            p = __ffma2_rn(make_float2(w[c].z, w[c].z), make_float2(b.x, b.y), p);
+            p = __ffma2_rn(make_float2(w[c].w, w[c].w), make_float2(b.z, b.w), p);
+            part[c * kPair + r] = p;
         }
     }
 }
 
 template <class S>
-__device__ __forceinline__ void fold(float *sum, float *comp, float *part) {
+__device__ __forceinline__ void fold(float2 *sum, float2 *comp, float2 *part) {
 #pragma unroll
-    for (int i = 0; i < S::C * kImg; ++i) {
-        kahan(&sum[i], &comp[i], part[i]);
-        part[i] = 0.0f;
+    for (int i = 0; i < S::C * kPair; ++i) {
+        kahan2(sum[i], comp[i], part[i]);
+        part[i] = make_float2(0.0f, 0.0f);
+    }
+}
+
+// Stage the sixteen image sequences of input positions s0 .. s0 + span - 1 as
+// eight (north, south) pairs: pair r < 4 holds quarter turn r of the direct
+// images, pair 4 + r of the reflected ones; element (r, j) at st[2 (r kStride + j)].
+template <class S, bool MIRROR>
+__device__ __forceinline__ void stage(const SymRing &g, const float *__restrict__ m, float *st,
+                                      int s0, int span) {
+    constexpr int kStride = S::kStride;
+    const int L2 = g.len, Q2 = L2 / 4;
+    for (int j = threadIdx.x; j < span; j += S::T) {
+        const int kp = s0 + j;
+        const int idx = sym_pmod(kp, L2);
+        const int idr = sym_pmod(Q2 - kp - g.phase, L2);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            int ia = idx + qq * Q2;
+            if (ia >= L2) ia -= L2;
+            int ib = idr + qq * Q2;
+            if (ib >= L2) ib -= L2;
+            const float an = __ldg(m + g.start + ia), bn = __ldg(m + g.start + ib);
+            const float as = MIRROR ? __ldg(m + g.start_m + ia) : 0.0f;
+            const float bs = MIRROR ? __ldg(m + g.start_m + ib) : 0.0f;
+            *reinterpret_cast<float2 *>(st + 2 * (qq * kStride + j)) = make_float2(an, as);
+            *reinterpret_cast<float2 *>(st + 2 * ((4 + qq) * kStride + j)) = make_float2(bn, bs);
+        }
     }
 }
 
@@ -211,18 +247,16 @@ __device__ __forceinline__ void quad_mixed(const float4 *xt, OddPos &sp, OddPos 
 }
 
 // Quads j in [ja, jb) of one regime for this lane's quarter (first position
-// p0 = QA4 + 4 ja, local offset in the staged segment p0 - s0).  Software-
-// pipelined: the next quad's weights are looked up while the current quad's
-// FFMAs run.
+// p0 = QA4 + 4 ja, local offset in the staged segment p0 - s0).
 template <class S, bool MIRROR, int SIGN>
 __device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int loc, int nquads,
-                                         OddPos s, const OddStep &k, const int *kk, float *sum,
-                                         float *comp, float *part, int &nfold) {
+                                         OddPos s, const OddStep &k, const int *kk, float2 *sum,
+                                         float2 *comp, float2 *part, int &nfold) {
     constexpr int C = S::C;
     for (int q = 0; q < nquads; ++q) {
         float4 w[C];
         quad_fast<C, SIGN>(xt, s, k, kk, w);
-        fma_quad<S, MIRROR>(st, loc, w, part);
+        fma_quad<S>(st, loc, w, part);
         loc += 4;
         if (++nfold == kFold) {
             nfold = 0;
@@ -234,13 +268,13 @@ __device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int 
 template <class S, bool MIRROR>
 __device__ __forceinline__ void run_mixed(const float4 *xt, const float *st, int loc, int nquads,
                                           OddPos sp, OddPos sn, int NQ, int Dl, const OddStep &k,
-                                          const int *kk, int thr0, float *sum, float *comp,
-                                          float *part, int &nfold) {
+                                          const int *kk, int thr0, float2 *sum, float2 *comp,
+                                          float2 *part, int &nfold) {
     constexpr int C = S::C;
     for (int q = 0; q < nquads; ++q) {
         float4 w[C];
         quad_mixed<C>(xt, sp, sn, NQ, Dl, k, kk, thr0, w);
-        fma_quad<S, MIRROR>(st, loc, w, part);
+        fma_quad<S>(st, loc, w, part);
         loc += 4;
         if (++nfold == kFold) {
             nfold = 0;
@@ -256,11 +290,11 @@ template <class S, bool MIRROR>
 __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &g, int c0,
                                               int n_cls, int t, int L,
                                               const float *__restrict__ m, float *st,
-                                              float4 *xt, int *sW, float *sum, float *comp,
-                                              float *part) {
-    constexpr int T = S::T, C = S::C, kSpan = S::kSpan, kStride = S::kStride, NW = T / 32;
+                                              float4 *xt, int *sW, float2 *sum, float2 *comp,
+                                              float2 *part) {
+    constexpr int T = S::T, C = S::C, kSpan = S::kSpan, NW = T / 32;
     const int tid = threadIdx.x, wid = tid >> 5, ql = tid & 7;
-    const int L2 = g.len, Q2 = L2 / 4;
+    const int L2 = g.len;
     const int D = 2 * L2, Dl = 2 * L;
     const int ncut = g.oncut;
     // this lane's quarter: classes kQ .. kQ + 8 C - 1 (those below n_cls exist); class
@@ -331,25 +365,7 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
     const bool single = hi - lo + 1 <= kSpan;  // one segment: no reduction between segments
     for (int s0 = lo;;) {
         const int span = min(kSpan, ((hi - s0 + 1) + 3) & ~3);
-        // stage the sixteen image sequences of positions s0 .. s0 + span - 1
-        for (int j = tid; j < span; j += T) {
-            const int kp = s0 + j;
-            const int idx = sym_pmod(kp, L2);
-            const int idr = sym_pmod(Q2 - kp - g.phase, L2);
-#pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                int ia = idx + qq * Q2;
-                if (ia >= L2) ia -= L2;
-                int ib = idr + qq * Q2;
-                if (ib >= L2) ib -= L2;
-                st[qq * kStride + j] = __ldg(m + g.start + ia);
-                st[(8 + qq) * kStride + j] = __ldg(m + g.start + ib);
-                if constexpr (MIRROR) {
-                    st[(4 + qq) * kStride + j] = __ldg(m + g.start_m + ia);
-                    st[(12 + qq) * kStride + j] = __ldg(m + g.start_m + ib);
-                }
-            }
-        }
+        stage<S, MIRROR>(g, m, st, s0, span);
         __syncthreads();
         // quads of this warp inside the segment: every quarter's quad within it
         int jB = jnext;
@@ -411,28 +427,30 @@ __device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing 
 
 // Positions a..b of one segment for classes c = 0..C-1 with windows
 // [lo[c], hi[c]] (num of class c = num0 + 2 c L2).
-template <class S, bool MIRROR, int MODE>
+template <class S, int MODE>
 __device__ __forceinline__ void acc_pairs(const ConvPlan &P, const SymRing &g, const float *st,
                                           int s0, int a, int b, long long num0, int L,
-                                          const int *lo, const int *hi, float *sum, float *comp,
-                                          float *part) {
+                                          const int *lo, const int *hi, float2 *sum, float2 *comp,
+                                          float2 *part) {
     constexpr int C = S::C;
     int nq = 0;
     for (int kq = s0 + ((a - s0) & ~3); kq <= b; kq += 4) {
         // (rare: one class at a time, each loading the images again)
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const float4 w = quad_weights<MODE>(P, g, kq, lo[c], hi[c], num0 + 2LL * c * g.len, L);
+            float4 w[C];
+            w[0] = quad_weights<MODE>(P, g, kq, lo[c], hi[c], num0 + 2LL * c * g.len, L);
 #pragma unroll
-            for (int i = 0; i < kImg; ++i) {
-                if (!MIRROR && (i & 4)) continue;
-                const float4 v = *reinterpret_cast<const float4 *>(st + i * S::kStride + kq - s0);
-                float pp = part[c * kImg + i];
-                pp = fmaf(w.x, v.x, pp);
-                pp = fmaf(w.y, v.y, pp);
-                pp = fmaf(w.z, v.z, pp);
-                pp = fmaf(w.w, v.w, pp);
-                part[c * kImg + i] = pp;
+            for (int r = 0; r < kPair; ++r) {
+                const float *row = st + r * 2 * S::kStride + 2 * (kq - s0);
+                const float4 va = *reinterpret_cast<const float4 *>(row);
+                const float4 vb = *reinterpret_cast<const float4 *>(row + 4);
+                float2 p = part[c * kPair + r];
+                p = __ffma2_rn(make_float2(w[0].x, w[0].x), make_float2(va.x, va.y), p);
+                p = __ffma2_rn(make_float2(w[0].y, w[0].y), make_float2(va.z, va.w), p);
+                p = __ffma2_rn(make_float2(w[0].z, w[0].z), make_float2(vb.x, vb.y), p);
+                p = __ffma2_rn(make_float2(w[0].w, w[0].w), make_float2(vb.z, vb.w), p);
+                part[c * kPair + r] = p;
             }
         }
         if (++nq == kFold) {
@@ -449,7 +467,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                                          int band_hi, const float *__restrict__ m,
                                          float *__restrict__ o, SymRing *sR, float *st,
                                          float4 *xt, int *sW, int *__restrict__ err) {
-    constexpr int T = S::T, C = S::C, kSpan = S::kSpan, kStride = S::kStride;
+    constexpr int C = S::C, kSpan = S::kSpan;
     const int tid = threadIdx.x;
     const DevRing R = P.d_rings[r];
     const int L = R.len, Q = L / 4, t = R.phase;
@@ -457,9 +475,10 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
     const int k0 = c0 + C * tid;  // this thread's first class
     const bool active = k0 < n_cls;
     const int k_first = c0, k_last = min(c0 + S::kClasses, n_cls) - 1;
-    float sum[C * kImg], comp[C * kImg], part[C * kImg];
+    float2 sum[C * kPair], comp[C * kPair], part[C * kPair];  // .x north, .y south images
 #pragma unroll
-    for (int i = 0; i < C * kImg; ++i) sum[i] = comp[i] = part[i] = 0.0f;
+    for (int i = 0; i < C * kPair; ++i)
+        sum[i] = comp[i] = part[i] = make_float2(0.0f, 0.0f);
 
     for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
         const int nq = min(kRingChunk, rg.y - q0 + 1);
@@ -469,7 +488,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
         for (int qi = 0; qi < nq; ++qi) {
             const SymRing g = sR[qi];
             if (g.hw < 0.0f) continue;
-            const int L2 = g.len, Q2 = L2 / 4;
+            const int L2 = g.len;
             // invariant the arithmetic relies on (the host's split construction
             // guarantees it): class integers fit in int32
             if (tid == 0 &&
@@ -495,24 +514,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 // positions this segment needs (the union ends at U1)
                 const int span = min(kSpan, ((U1 - s0 + 1) + 3) & ~3);
                 __syncthreads();  // the previous segment is consumed
-                for (int j = tid; j < span; j += T) {
-                    const int kp = s0 + j;
-                    const int idx = sym_pmod(kp, L2);
-                    const int idr = sym_pmod(Q2 - kp - g.phase, L2);
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        int ia = idx + qq * Q2;
-                        if (ia >= L2) ia -= L2;
-                        int ib = idr + qq * Q2;
-                        if (ib >= L2) ib -= L2;
-                        st[qq * kStride + j] = __ldg(m + g.start + ia);
-                        st[(8 + qq) * kStride + j] = __ldg(m + g.start + ib);
-                        if constexpr (MIRROR) {
-                            st[(4 + qq) * kStride + j] = __ldg(m + g.start_m + ia);
-                            st[(12 + qq) * kStride + j] = __ldg(m + g.start_m + ib);
-                        }
-                    }
-                }
+                stage<S, MIRROR>(g, m, st, s0, span);
                 __syncthreads();
                 if (!active) continue;
                 const int a = max(wa, s0), b = min(wb, s0 + span - 1);
@@ -520,9 +522,9 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 // (classes without a reflection partner accumulate the reflected
                 // images too; those sums are never written)
                 if (g.small)
-                    acc_pairs<S, MIRROR, 1>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
+                    acc_pairs<S, 1>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
                 else
-                    acc_pairs<S, MIRROR, 0>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
+                    acc_pairs<S, 0>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
             }
         }
     }
@@ -544,13 +546,13 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int kq = kk + qq * Q;
-                const float vn = sum[cl * kImg + 8 * c + qq] * P.domega;
+                const float vn = sum[cl * kPair + 4 * c + qq].x * P.domega;
                 if (wn) {
                     if (add) o[R.start + kq] += vn;
                     else o[R.start + kq] = vn;
                 }
                 if constexpr (MIRROR) {
-                    const float vs = sum[cl * kImg + 8 * c + 4 + qq] * P.domega;
+                    const float vs = sum[cl * kPair + 4 * c + qq].y * P.domega;
                     if (ws) {
                         if (add) o[start_s + kq] += vs;
                         else o[start_s + kq] = vs;
