@@ -181,7 +181,7 @@ def eq6_alpha_refit():
 
 
 def _split_choice():
-    """The measured split selection tests/split_choice.py recorded on the GPU machine, or {}."""
+    """The measured split selection tests/split_choice.py recorded on the machine with the GPU, or {}."""
     try:
         with open(SPLIT_CHOICE) as f:
             return json.load(f)
@@ -228,7 +228,7 @@ def run_cheapest_split(K, torch, stream, b, cl, x):
     rec = _split_choice().get("c3", {})
     ch = rec.get("chosen")
     if not ch:
-        return {"source": "not measured (tests/split_choice.py writes it on the GPU box)"}
+        return {"source": "not measured (tests/split_choice.py writes it on the machine with the GPU)"}
     lcut, tc = int(ch["l_cut"]), ch["theta_cut_arcmin"] * ARC
     y = torch.empty_like(x)
     with K.make_split(b, 2048, lcut, tc, cl_in=cl) as sp:
@@ -282,7 +282,7 @@ def run_whole_split(K, torch, stream, b, cl, x):
 
 def split_accuracy(info):
     """eps_C of the benchmark's split (quoted from the measurement that
-    tests/split_accuracy.py writes on the GPU machine) and the Eq. 6 estimate with the
+    tests/split_accuracy.py writes on the machine with the GPU) and the Eq. 6 estimate with the
     paper's alpha = 5 and with alpha refitted so that Eq. 6 bounds every measured
     split of the surrogate's training set."""
     out = {"eq6_frac_error_alpha5": info["frac_error"]}

@@ -1,4 +1,4 @@
-"""Time the harmonic half of the split convolution on the host (run on the GPU machine's host):
+"""Time the harmonic half of the split convolution on the host (run on the host of the machine with the GPU):
 
     python tests/host_sht_costs.py [--out tests/golden/host_sht_times.csv]
 
@@ -49,7 +49,7 @@ def main():
         f.write("# Host time of the harmonic half (oracle ring SHT: analysis to l_cut, kernel\n")
         f.write(f"# applied, synthesis), written by tests/host_sht_costs.py on {os.cpu_count()} "
                 "host cores\n")
-        f.write("# of the GPU box; l_max = 2 nside (the map's band limit in Eq. 8's form).\n")
+        f.write("# of the machine with the GPU; l_max = 2 nside (the map's band limit in Eq. 8's form).\n")
         f.write("nside,lmax,l_cut,t_ms\n")
         for r in rows:
             f.write(f"{r[0]},{r[1]},{r[2]},{r[3]:.3f}\n")

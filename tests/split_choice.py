@@ -3,7 +3,7 @@
     python tests/split_choice.py [--out profiles/split_choice.json] [--only c2|c3]
 
 Sec. 2 picks a split by its cost model among the splits whose Eq. 6 estimate meets the
-error bound; this script adds a measured run as the judge: a candidate is accepted when the
+error bound; this script adds a measured run as the arbiter: a candidate is accepted when the
 fractional rms C_l error eps_C (Sec. 3) of the split convolution -- harmonic part by the
 oracle's synthesis plus the GPU real-space part -- against the full harmonic convolution of
 the same Gaussian random field (C_l = 1/(l+10)^2) is at most 1e-5.

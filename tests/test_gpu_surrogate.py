@@ -235,7 +235,7 @@ def test_surrogate_chosen_split_at_nside4096(K):
 @pytest.mark.skipif(not os.path.exists(DATA), reason="measured split data not generated")
 def test_selection_chain_falls_back_to_the_scan_and_a_measured_judge(K):
     """The selection chain of the surrogate (the network first, the Sec. 2 scan as the
-    fallback, a measured run as the judge) on a beam outside the network's confident
+    fallback, a measured run as the arbiter) on a beam outside the network's confident
     range: nside 128, a 110' beam (four pixel widths, inside the training beams), l_max
     256; the network asked for 1e-5 with a margin of five decades accepts nothing (-1),
     so the scan (ksc_scan_split: theta_cut 600'-3600' in 300' steps, l_cut searched, Eq. 6
@@ -269,7 +269,7 @@ def test_selection_chain_falls_back_to_the_scan_and_a_measured_judge(K):
     order = sorted((r for r in rows if r["l_cut"] >= 0),
                    key=lambda r: max(r["t_gpu_ms"], r["t_host_ms"]))
     assert order, "the scan must propose a split"
-    # the judge: measured eps_C of each proposal, cheapest first
+    # the arbiter: measured eps_C of each proposal, cheapest first
     ell = np.concatenate([np.arange(mm, lmax + 1) for mm in range(lmax + 1)])
     alm0 = inputs.grf_alm(lmax, cl, inputs.seed_for(5, 9000))
     m = O.alm2map(nside, alm0, lmax).astype(np.float32)

@@ -218,7 +218,7 @@ HOST_SHT = os.path.join(os.path.dirname(__file__), "golden", "host_sht_times.csv
                     reason="host SHT times not measured")
 def test_host_cost_refit_on_timed_host_sht(K):
     """The host half's cost model (Eq. 8's form, h0 + h1 l_cut^2 l_max / 4096^3) refitted to
-    the harmonic half timed on the GPU machine's host (tests/host_sht_costs.py): the library's
+    the harmonic half timed on the host of the machine with the GPU (tests/host_sht_costs.py): the library's
     relative least squares equals a plain least-squares solve of the same scaled system, the
     slope is positive, and the refit predicts the rows where the Legendre sums dominate
     (l_cut >= 512) to a median 35%."""
