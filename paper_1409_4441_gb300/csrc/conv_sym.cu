@@ -177,9 +177,9 @@ __device__ __forceinline__ OddPos odd_pos(int M, int D) {
 // Step constants: one position (N down by 2 L) moves PQ down and PN up by
 // (2 L m) / D = q1 + r1 / D.
 struct OddStep {
-    int q1, D2;    // D2 = 2 L' (N between consecutive classes)
+    int q1, q2, D2;    // D2 = 2 L' (N between consecutive classes)
     unsigned nct;  // the zero cell
-    float r1, Df, invD;
+    float r1, r2, Df, invD;
 };
 
 __device__ __forceinline__ void pos_down(OddPos &s, const OddStep &k) {
@@ -194,6 +194,18 @@ __device__ __forceinline__ void pos_up(OddPos &s, const OddStep &k) {
     s.R = b ? s.R - k.Df : s.R;
     s.a += k.q1 + (b ? 1 : 0);
 }
+__device__ __forceinline__ void pos_down2(OddPos &s, const OddStep &k) {
+    s.R -= k.r2;
+    const bool b = s.R < 0.0f;
+    s.R = b ? s.R + k.Df : s.R;
+    s.a -= k.q2 + (b ? 1 : 0);
+}
+__device__ __forceinline__ void pos_up2(OddPos &s, const OddStep &k) {
+    s.R += k.r2;
+    const bool b = s.R >= k.Df;
+    s.R = b ? s.R - k.Df : s.R;
+    s.a += k.q2 + (b ? 1 : 0);
+}
 
 __device__ __forceinline__ float odd_weight(const float4 *xt, int idx, unsigned nct, float f) {
     return hermite(xt[min((unsigned)idx, nct)], f);
@@ -205,19 +217,28 @@ __device__ __forceinline__ float odd_weight(const float4 *xt, int idx, unsigned 
 template <int C, int SIGN>
 __device__ __forceinline__ void quad_fast(const float4 *xt, OddPos &s, const OddStep &k,
                                           const int *kk, float4 *w) {
+    // positions 0..3 from the quad start with a dependence depth of two steps
+    OddPos p[4];
+    p[0] = s;
+    p[1] = s;
+    p[2] = s;
+    if (SIGN > 0) { pos_down(p[1], k); pos_down2(p[2], k); }
+    else { pos_up(p[1], k); pos_up2(p[2], k); }
+    p[3] = p[2];
+    s = p[2];
+    if (SIGN > 0) { pos_down(p[3], k); pos_down2(s, k); }
+    else { pos_up(p[3], k); pos_up2(s, k); }
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-        const float f = s.R * k.invD;
+        const float f = p[d].R * k.invD;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const float v = odd_weight(xt, SIGN > 0 ? s.a + kk[c] : s.a - kk[c], k.nct, f);
+            const float v = odd_weight(xt, SIGN > 0 ? p[d].a + kk[c] : p[d].a - kk[c], k.nct, f);
             if (d == 0) w[c].x = v;
             else if (d == 1) w[c].y = v;
             else if (d == 2) w[c].z = v;
             else w[c].w = v;
         }
-        if (SIGN > 0) pos_down(s, k);
-        else pos_up(s, k);
     }
 }
 
@@ -355,6 +376,8 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
         const int st1 = Dl * g.om;
         k.q1 = st1 / D;
         k.r1 = (float)(st1 - k.q1 * D);
+        k.q2 = (2 * st1) / D;
+        k.r2 = (float)(2 * st1 - k.q2 * D);
         k.Df = (float)D;
         k.D2 = D;
         k.invD = 1.0f / (float)D;
