@@ -52,7 +52,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the dominant kernel at the nside-2048 workload, from one ncu
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum, full launch);
 # absent until the current kernel has been captured
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {"conv_sym_kernel": 224318464 + 66258176}
 
 
 def workload_desc(extra=None):
