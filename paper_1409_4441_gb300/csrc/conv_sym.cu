@@ -45,7 +45,12 @@ namespace {
 constexpr int kRingChunk = 32;  // ring-pair constants staged per pass
 constexpr int kImg = 16;        // 4 rotations x {north, south} x {direct, reflected}
 constexpr int kPair = 8;        // image pairs (north, south mirror): FP32x2 operands
-constexpr int kFold = 16;       // quads per FP32 partial sum (64 positions)
+// FP32 partial sums fold into the compensated sums every kFold quads (64
+// positions), and every kFoldNear quads around the kernel's centre, where the
+// largest terms are: a term's partial then takes few roundings at its size.
+constexpr int kFold = 16;
+constexpr int kFoldNear = 2;
+constexpr int kFoldPair = 4;    // per-pair path: every 16 positions
 // Tile shape: T threads of C classes each, SPAN staged input positions per
 // segment (each image row padded by 4 floats), MINB resident CTAs per SM the
 // register budget is set for, XCAP table cells in dynamic shared memory.
@@ -60,13 +65,14 @@ using ShapeSmall = SymShape<128, 1, 448, 3, 2048>;  // variant 1: 128 classes, 3
 using ShapeWide = SymShape<128, 1, 448, 2, kXCap>;  // variant 2: 128 classes, full tables
 static_assert(ShapeC3::kSpan % 4 == 0 && ShapeSmall::kSpan % 4 == 0, "quad-aligned spans");
 
-// Kahan step on a pair of sums (every operation rounds to nearest, as in the
-// scalar form: v - c = fma(c, -1, v) and (t - s) - y = fma(y, -1, fma(s, -1, t))).
-__device__ __forceinline__ void kahan2(float2 &sum, float2 &comp, float2 v) {
+// Kahan step on a pair of sums, with the compensation carried in the partial:
+// the partial starts from the low part the previous step lost (rather than
+// from zero), so one step is t = s + p, p = p - (t - s), s = t, every operation
+// rounded to nearest (t - s = fma(s, -1, t)).
+__device__ __forceinline__ void kahan2(float2 &sum, float2 &part) {
     const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 y = __ffma2_rn(comp, m1, v);
-    const float2 t = __fadd2_rn(sum, y);
-    comp = __ffma2_rn(y, m1, __ffma2_rn(sum, m1, t));
+    const float2 t = __fadd2_rn(sum, part);
+    part = __ffma2_rn(__ffma2_rn(sum, m1, t), m1, part);
     sum = t;
 }
 
@@ -106,12 +112,9 @@ __device__ __forceinline__ void fma_quad(const float *st, int j, const float4 *w
 }
 
 template <class S>
-__device__ __forceinline__ void fold(float2 *sum, float2 *comp, float2 *part) {
+__device__ __forceinline__ void fold(float2 *sum, float2 *part) {
 #pragma unroll
-    for (int i = 0; i < S::C * kPair; ++i) {
-        kahan2(sum[i], comp[i], part[i]);
-        part[i] = make_float2(0.0f, 0.0f);
-    }
+    for (int i = 0; i < S::C * kPair; ++i) kahan2(sum[i], part[i]);
 }
 
 // Stage the sixteen image sequences of input positions s0 .. s0 + span - 1 as
@@ -272,7 +275,7 @@ __device__ __forceinline__ void quad_mixed(const float4 *xt, OddPos &sp, OddPos 
 template <class S, bool MIRROR, int SIGN>
 __device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int loc, int nquads,
                                          OddPos s, const OddStep &k, const int *kk, float2 *sum,
-                                         float2 *comp, float2 *part, int &nfold) {
+                                         float2 *part, int &nfold) {
     constexpr int C = S::C;
     for (int q = 0; q < nquads; ++q) {
         float4 w[C];
@@ -281,7 +284,7 @@ __device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int 
         loc += 4;
         if (++nfold == kFold) {
             nfold = 0;
-            fold<S>(sum, comp, part);
+            fold<S>(sum, part);
         }
     }
 }
@@ -289,19 +292,22 @@ __device__ __forceinline__ void run_fast(const float4 *xt, const float *st, int 
 template <class S, bool MIRROR>
 __device__ __forceinline__ void run_mixed(const float4 *xt, const float *st, int loc, int nquads,
                                           OddPos sp, OddPos sn, int NQ, int Dl, const OddStep &k,
-                                          const int *kk, int thr0, float2 *sum, float2 *comp,
+                                          const int *kk, int thr0, float2 *sum,
                                           float2 *part, int &nfold) {
     constexpr int C = S::C;
+    // the quads where some lane's N changes sign hold every lane's centre: the
+    // partial before them ends here, theirs fold every kFoldNear quads, and the
+    // next kFoldNear quads (the last lanes' terms just past the centre) end theirs
+    fold<S>(sum, part);
     for (int q = 0; q < nquads; ++q) {
         float4 w[C];
         quad_mixed<C>(xt, sp, sn, NQ, Dl, k, kk, thr0, w);
         fma_quad<S>(st, loc, w, part);
         loc += 4;
-        if (++nfold == kFold) {
-            nfold = 0;
-            fold<S>(sum, comp, part);
-        }
+        if ((q + 1) % kFoldNear == 0) fold<S>(sum, part);
     }
+    if (nquads % kFoldNear != 0) fold<S>(sum, part);
+    nfold = kFold - kFoldNear;
 }
 
 // One ring pair through the lockstep path.  Returns false (before any work, and
@@ -311,7 +317,7 @@ template <class S, bool MIRROR>
 __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &g, int c0,
                                               int n_cls, int t, int L,
                                               const float *__restrict__ m, float *st,
-                                              float4 *xt, int *sW, float2 *sum, float2 *comp,
+                                              float4 *xt, int *sW, float2 *sum,
                                               float2 *part) {
     constexpr int T = S::T, C = S::C, kSpan = S::kSpan, NW = T / 32;
     const int tid = threadIdx.x, wid = tid >> 5, ql = tid & 7;
@@ -402,19 +408,19 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
             if (e1 > jnext) {
                 const int NQ = NQ0 - 4 * Dl * jnext;
                 run_fast<S, MIRROR, 1>(xt, st, loc0, e1 - jnext, odd_pos(NQ * g.om + g.ooff, D),
-                                       k, kk, sum, comp, part, nfold);
+                                       k, kk, sum, part, nfold);
             }
             if (e2 > e1) {
                 const int NQ = NQ0 - 4 * Dl * e1;
                 run_mixed<S, MIRROR>(xt, st, loc0 + 4 * (e1 - jnext), e2 - e1,
                                      odd_pos(NQ * g.om + g.ooff, D),
                                      odd_pos(-NQ * g.om + g.ooff, D), NQ, Dl, k, kk, thr0, sum,
-                                     comp, part, nfold);
+                                     part, nfold);
             }
             if (jB > e2) {
                 const int NQ = NQ0 - 4 * Dl * e2;
                 run_fast<S, MIRROR, -1>(xt, st, loc0 + 4 * (e2 - jnext), jB - e2,
-                                        odd_pos(-NQ * g.om + g.ooff, D), k, kk, sum, comp, part,
+                                        odd_pos(-NQ * g.om + g.ooff, D), k, kk, sum, part,
                                         nfold);
             }
         }
@@ -430,7 +436,7 @@ __device__ __forceinline__ bool lockstep_pair(const ConvPlan &P, const SymRing &
         __syncthreads();  // every thread has read sW and consumed the segment
         s0 = nxt;
     }
-    fold<S>(sum, comp, part);
+    fold<S>(sum, part);
     return true;
 }
 
@@ -453,7 +459,7 @@ __device__ __forceinline__ float4 quad_weights(const ConvPlan &P, const SymRing 
 template <class S, int MODE>
 __device__ __forceinline__ void acc_pairs(const ConvPlan &P, const SymRing &g, const float *st,
                                           int s0, int a, int b, long long num0, int L,
-                                          const int *lo, const int *hi, float2 *sum, float2 *comp,
+                                          const int *lo, const int *hi, float2 *sum,
                                           float2 *part) {
     constexpr int C = S::C;
     int nq = 0;
@@ -476,12 +482,12 @@ __device__ __forceinline__ void acc_pairs(const ConvPlan &P, const SymRing &g, c
                 part[c * kPair + r] = p;
             }
         }
-        if (++nq == kFold) {
+        if (++nq == kFoldPair) {
             nq = 0;
-            fold<S>(sum, comp, part);
+            fold<S>(sum, part);
         }
     }
-    fold<S>(sum, comp, part);
+    fold<S>(sum, part);
 }
 
 template <class S, bool MIRROR>
@@ -498,10 +504,10 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
     const int k0 = c0 + C * tid;  // this thread's first class
     const bool active = k0 < n_cls;
     const int k_first = c0, k_last = min(c0 + S::kClasses, n_cls) - 1;
-    float2 sum[C * kPair], comp[C * kPair], part[C * kPair];  // .x north, .y south images
+    float2 sum[C * kPair], part[C * kPair];  // .x north, .y south images
 #pragma unroll
     for (int i = 0; i < C * kPair; ++i)
-        sum[i] = comp[i] = part[i] = make_float2(0.0f, 0.0f);
+        sum[i] = part[i] = make_float2(0.0f, 0.0f);
 
     for (int q0 = rg.x; q0 <= rg.y; q0 += kRingChunk) {
         const int nq = min(kRingChunk, rg.y - q0 + 1);
@@ -519,7 +525,7 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 atomicExch(err, KSC_ERR_DEVICE_BOUNDS);
             // the odd-step table, when the ring pair has one that fits
             if (g.onct > 0 && g.onct + 1 <= S::kXCap &&
-                lockstep_pair<S, MIRROR>(P, g, c0, n_cls, t, L, m, st, xt, sW, sum, comp, part))
+                lockstep_pair<S, MIRROR>(P, g, c0, n_cls, t, L, m, st, xt, sW, sum, part))
                 continue;
             // per-pair weights: the union of this thread's classes' windows
             long long num0, numx;
@@ -545,12 +551,15 @@ __device__ __forceinline__ void sym_item(const ConvPlan &P, int r, int c0, int n
                 // (classes without a reflection partner accumulate the reflected
                 // images too; those sums are never written)
                 if (g.small)
-                    acc_pairs<S, 1>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
+                    acc_pairs<S, 1>(P, g, st, s0, a, b, num0, L, lo, hi, sum, part);
                 else
-                    acc_pairs<S, 0>(P, g, st, s0, a, b, num0, L, lo, hi, sum, comp, part);
+                    acc_pairs<S, 0>(P, g, st, s0, a, b, num0, L, lo, hi, sum, part);
             }
         }
     }
+    // the sums with the low parts their last steps carried
+#pragma unroll
+    for (int i = 0; i < C * kPair; ++i) sum[i] = __fadd2_rn(sum[i], part[i]);
     const int rs = P.nrings - 1 - r;
     const int start_s = P.d_rings[rs].start;
     const bool wn = r >= band_lo && r <= band_hi;
