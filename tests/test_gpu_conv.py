@@ -201,6 +201,31 @@ def test_nside2048_sampled_parity(K, tc_arcmin):
     _check(got[pix], ref, amb)
 
 
+def test_nside2048_worst_pixels(K):
+    """The same workload over the whole map: the pixels where the table path and the
+    exact-weight path (exact_weights = 1) differ most are where FP32 rounding is largest.
+    Both paths must be within tolerance of the oracle there, with the rms taken over
+    sampled pixels."""
+    nside, lmax, lcut = 2048, 4096, 1024
+    tc = 240 * ARC
+    c = inputs.gaussian_beam(lmax, 5 * ARC)
+    c[: lcut + 1] = 0.0
+    m = inputs.white_noise_map(nside, inputs.seed_for(3)).astype(np.float32)
+    got = []
+    for ew in (0, 1):
+        with K.make_split_real(c, nside, tc, exact_weights=ew) as sp:
+            n_int = K.split_info(sp)["n_intervals"]
+            got.append(_run(K, sp, m))
+    worst = np.argsort(np.abs(got[0] - got[1]))[::-1][:24]
+    pix = np.concatenate([inputs.sample_pixels(nside, 200, 29), worst])
+    ref, amb = O.brute_conv(nside, m.astype(np.float64), tc, table=O.hermite_nodes(c, tc, n_int),
+                            out_pix=pix)
+    rms = np.sqrt(np.mean(ref[:200] ** 2))
+    for g in got:
+        err = np.abs(g[pix] - ref)
+        assert (err <= 1e-6 * rms + amb).all(), (err.max() / rms, pix[np.argmax(err)])
+
+
 def test_bands_multimap_host_bitwise_and_batch(K):
     nside = 32
     tc = np.radians(8.0)
