@@ -31,8 +31,8 @@
 // test; four positions of a thread then take one 16-byte shared load per image
 // feeding 4 C FFMAs.  Ring pairs without a table (whole-ring windows, or more
 // cells than a CTA holds) evaluate the double-float chord and the K_r table per
-// pair (ksc_device.cuh).  FP32 partial sums over 64 positions are Kahan-folded
-// into the totals.
+// pair (ksc_device.cuh).  FP32 partial sums are Kahan-folded into the totals
+// every 64 positions, and every 8 around the kernel's centre.
 #include <cstdint>
 
 #include "ksc_device.cuh"
