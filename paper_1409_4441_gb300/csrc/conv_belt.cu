@@ -74,6 +74,57 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+// Kahan step: sum + comp carries the total, v is the next partial sum.
+__device__ __forceinline__ void kahan(float &sum, float &comp, float v) {
+    const float y = v - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// One block of 2 kU steps of the sliding window, acc[u] += w[j] seg[u + j] for
+// j in [j0, j0 + 2 kU), then acc into the ring partial.  On entry values
+// j0 .. j0 + kU - 2 of the segment sit in R0[0 .. kU - 2]; on exit values
+// j0 + 2 kU .. j0 + 3 kU - 2 do.
+// With MID_FOLD the ring partial and the first half's steps are folded into the
+// totals (sum, comp) between the two halves.
+template <bool MID_FOLD>
+__device__ __forceinline__ void belt_block(const float *sg, const float *wbuf, int j0,
+                                           float (&R0)[2 * kU], float (&acc)[kU],
+                                           float (&ring)[kU], float (&sum)[kU],
+                                           float (&comp)[kU]) {
+    // block A: values j0 .. j0 + 2kU - 2 live in R0[(v) % 2kU]
+#pragma unroll
+    for (int e = kU - 1; e < 2 * kU - 1; ++e) R0[e] = sg[j0 + e];
+#pragma unroll
+    for (int jj = 0; jj < kU; ++jj) {
+        const float wv = wbuf[j0 + jj];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) acc[u] = fmaf(wv, R0[u + jj], acc[u]);
+    }
+    if constexpr (MID_FOLD) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            kahan(sum[u], comp[u], ring[u] + acc[u]);
+            acc[u] = ring[u] = 0.0f;
+        }
+    }
+    // block B: values j0 + kU .. j0 + 3kU - 2 -> R0[(v - j0) % 2kU]
+#pragma unroll
+    for (int e = 2 * kU - 1; e < 3 * kU - 1; ++e) R0[e % (2 * kU)] = sg[j0 + e];
+#pragma unroll
+    for (int jj = 0; jj < kU; ++jj) {
+        const float wv = wbuf[j0 + kU + jj];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) acc[u] = fmaf(wv, R0[(kU + u + jj) % (2 * kU)], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        ring[u] += acc[u];
+        acc[u] = 0.0f;
+    }
+}
+
 struct PairGeom {
     DF A, B, c1;        // (chord n_int/d_cut)^2 = A + B sin^2(x), x = (t - t' - 2 Delta) c1
     int d0;             // first Delta of the padded window
@@ -196,40 +247,33 @@ __device__ __forceinline__ bool belt_item(const ConvPlan &P, int r, int k0,
         float R0[2 * kU];
 #pragma unroll
         for (int e = 0; e < kU - 1; ++e) R0[e] = sg[e];
-        for (int j0 = 0; j0 < g.nd; j0 += 2 * kU) {
-            // block A: values j0 .. j0 + 2kU - 2 live in R0[(v) % 2kU]
+        // The largest terms of a ring pair lie at its closest approach, Delta in
+        // [-2, 3] (step j = 3 - d0 the last of them).  Where that approach is within
+        // an eighth of the cut, the ring partial is folded into the totals right
+        // after the half block (kU steps) holding j = 3 - d0, so that the later
+        // steps do not round at the size of those terms.  That block runs apart
+        // from the two loops around it, which stay free of the test.
+        const bool near = g.A.h < P.nint2 * (1.0f / 64.0f);
+        const int jpk = 3 - g.d0;
+        const int jb = near ? min(g.nd, (jpk / (2 * kU)) * (2 * kU)) : g.nd;
+        int j0 = 0;
+        for (; j0 < jb; j0 += 2 * kU) belt_block<false>(sg, wbuf, j0, R0, acc, ring, sum, comp);
+        if (j0 < g.nd) {
+            if (jpk - j0 < kU) {
+                belt_block<true>(sg, wbuf, j0, R0, acc, ring, sum, comp);
+            } else {
+                belt_block<false>(sg, wbuf, j0, R0, acc, ring, sum, comp);
 #pragma unroll
-            for (int e = kU - 1; e < 2 * kU - 1; ++e) R0[e] = sg[j0 + e];
-#pragma unroll
-            for (int jj = 0; jj < kU; ++jj) {
-                const float wv = wbuf[j0 + jj];
-#pragma unroll
-                for (int u = 0; u < kU; ++u) acc[u] = fmaf(wv, R0[u + jj], acc[u]);
+                for (int u = 0; u < kU; ++u) {
+                    kahan(sum[u], comp[u], ring[u]);
+                    ring[u] = 0.0f;
+                }
             }
-            // block B: values j0 + kU .. j0 + 3kU - 2 -> R0[(v - j0) % 2kU]
-#pragma unroll
-            for (int e = 2 * kU - 1; e < 3 * kU - 1; ++e) R0[e % (2 * kU)] = sg[j0 + e];
-#pragma unroll
-            for (int jj = 0; jj < kU; ++jj) {
-                const float wv = wbuf[j0 + kU + jj];
-#pragma unroll
-                for (int u = 0; u < kU; ++u)
-                    acc[u] = fmaf(wv, R0[(kU + u + jj) % (2 * kU)], acc[u]);
-            }
-            // values j0 + 2kU .. j0 + 3kU - 2 already sit at R0[0 .. kU-2]
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                ring[u] += acc[u];
-                acc[u] = 0.0f;
-            }
+            j0 += 2 * kU;
         }
+        for (; j0 < g.nd; j0 += 2 * kU) belt_block<false>(sg, wbuf, j0, R0, acc, ring, sum, comp);
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const float y = ring[u] - comp[u];
-            const float t = sum[u] + y;
-            comp[u] = (t - sum[u]) - y;
-            sum[u] = t;
-        }
+        for (int u = 0; u < kU; ++u) kahan(sum[u], comp[u], ring[u]);
     }
     __syncthreads();
     if (*s_abort) {
