@@ -19,7 +19,9 @@
 //      in registers; a block of kU weights and 2kU-1 inputs gives kU*kU FFMAs
 //      for 2kU shared-memory loads.  kU is odd, so the kU-word stride between
 //      lanes hits 32 distinct banks.
-//   4. folds the FP32 ring partial sums into the totals with Kahan steps.
+//   4. folds the FP32 ring partial sums into the totals with Kahan steps, at
+//      the end of the ring pair and, where the pair's closest approach is near,
+//      right after the half block that holds its largest terms.
 // Every mbarrier wait is bounded; a wait that runs out raises a device error
 // flag and the kernel stops work instead of hanging.
 #include <algorithm>
